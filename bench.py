@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of one dynamic frame of the voxel ray-tracing path.
+
+Workload (default): tractography-like bundles -- 100k streamlines x 100
+vertices (9.9M segments) in 30 bundles inside an ellipsoid, 256^3 grid, tube
+radius 0.35 voxel, 1920x1080 perspective camera, opacity 0.3 with full ordered
+compositing, culling on; each frame 5% of the streamlines are replaced
+(interactive filtering). A step = update of the replaced vertices + ingest +
+voxelize pass 1 + mips + cull marks + scan + pass 2 + trace (+ repair rounds).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload bundles|walks|abc]
+
+Prints ONE JSON line (rank 0). Under torchrun each rank renders its own replica
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/frame (voxelize+cull+trace) at 1080p, 10M segs; p50/p99 served-frame latency"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- workloads
+def make_workload(name):
+    from gen import linesets as G
+    if name == "bundles":
+        bs = G.bundles()
+        cam = G.bundles_camera()
+        upd = lambda f: G.bundles_update(bs, f)  # noqa: E731
+        return dict(ls=bs.lineset, cam=cam, update=upd, alpha=0.3, ao=0, cull=1,
+                    desc=("tractography-like bundles: 100k streamlines x 100 vertices "
+                          "(9.9M segments), 30 bundles, grid 256^3, r 0.35, 1920x1080 "
+                          "perspective, alpha 0.3 ordered compositing, culling on, 5% of "
+                          "streamlines replaced per frame"))
+    if name == "walks":
+        ls = G.tiny_walks()
+        cam = G.tiny_walks_camera()
+        rng = np.random.default_rng(7)
+
+        def upd(f):
+            k = ls.n_vertices // 20
+            first = (f * k) % (ls.n_vertices - k)
+            return first, (ls.xyz[first:first + k] + rng.normal(0, 0.05, (k, 3))).astype(np.float32)
+        return dict(ls=ls, cam=cam, update=upd, alpha=1.0, ao=0, cull=0,
+                    desc="random walks: 2000 x 50 vertices, grid 64^3, r 0.4, 256x256 ortho, opaque")
+    if name == "abc":
+        ls = G.abc_pathlines(frame=0)
+        cam = G.abc_camera(frame=0)
+
+        def upd(f):
+            nl = G.abc_pathlines(frame=f + 1)
+            return 0, nl.xyz
+        return dict(ls=ls, cam=cam, update=upd, alpha=1.0, ao=6, cull=1,
+                    desc=("ABC-flow lines: 1M x 32 vertices (31M segments), grid 512^3, r 0.25, "
+                          "1920x1080 perspective from the centre, opaque, 6-cone AO, culling on, "
+                          "every vertex moves per frame"))
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        try:
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- roofline
+def stage_bytes(stage, n, V, st, px):
+    """Algorithmic (compulsory) DRAM bytes of one launch of a stage's kernels."""
+    N3 = n ** 3
+    F, Fv = st["fragments"], st["fragments_listed"]
+    return {
+        "ingest": 12 * V + V + 32 * V,                 # raw xyz + flags in, pos + clip normal out
+        "pass1": 32 * V + 4 * N3,                      # pos + normal in, packed words written back
+        "mips": 4 * N3 + 4 * N3 * 8 // 7,              # words in, pyramid out
+        "cull": 4 * N3 + N3 + N3 // 8,                 # words in, eroded + marks out
+        "scan": 4 * N3 + N3 // 8 + 4 * N3,             # words + marks in, offsets out
+        "pass2": 16 * V + 4 * Fv + 4 * N3,             # pos in, list entries + cursors out
+        "trace": 24 * px,                              # rgba + first id + first depth out
+        "repair": 0,
+    }[stage]
+
+
+def hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_baseline(wl, budget_s=20.0):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload:
+    lists for a 1% sample of the polylines (scaled x100) plus the render of every
+    64th pixel of that sampled scene (scaled x64)."""
+    import oracle
+    from gen.linesets import LineSet
+    ls = wl["ls"]
+    P = ls.n_polylines
+    step = 100 if P >= 1000 else 1
+    keep = np.arange(0, P, step)
+    lens = np.diff(ls.offsets)[keep]
+    starts = ls.offsets[keep]
+    xyz = np.concatenate([ls.xyz[s:s + l] for s, l in zip(starts, lens)], 0)
+    sub = LineSet(xyz=xyz, offsets=np.concatenate([[0], np.cumsum(lens)]), n=ls.n, radius=ls.radius)
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle.from_lineset(sub, nthreads=cores)
+    t0 = time.perf_counter()
+    o.build_lists()
+    t_lists = time.perf_counter() - t0
+    cam = wl["cam"]
+    npx = cam.width * cam.height
+    pstep = 64
+    t0 = time.perf_counter()
+    done = 0
+    # render whole rows, every 64th row, to keep the sample spatially spread
+    for row in range(0, cam.height, pstep):
+        o.render(cam, alpha=wl["alpha"], ao_cones=wl["ao"], pix_begin=row * cam.width,
+                 pix_end=(row + 1) * cam.width)
+        done += cam.width
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t_render = time.perf_counter() - t0
+    ms = 1e3 * (t_lists * step + t_render * npx / max(done, 1))
+    return {"value": ms, "unit": "ms/frame", "cores": cores, "kind": "oracle",
+            "sample": (f"lists of every {step}th polyline ({sub.n_segments} segments, x{step}) "
+                       f"+ render of {done} pixels of that sampled scene (x{npx / max(done, 1):.0f}); "
+                       "the sampled scene is sparser than the full one, so the render part is "
+                       "a lower bound")}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2510_09081_gb300 as vrt
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.time()
+    wl = make_workload(args.workload)
+    ls, cam = wl["ls"], wl["cam"]
+    log(f"[bench] workload ready in {time.time() - t0:.1f}s: V={ls.n_vertices} S={ls.n_segments}")
+    n_upd = max(1, min(args.steps + args.warmup, 4))
+    upd_host, upd_dev = [], []
+    for f in range(n_upd):
+        first, blk = wl["update"](f)
+        h = torch.from_numpy(np.ascontiguousarray(blk, np.float32)).pin_memory()
+        upd_host.append((first, h))
+        upd_dev.append((first, h.to(dev)))
+    r = vrt.Renderer(ls.n, ls.radius, stream=stream)
+    xyz_dev = torch.from_numpy(ls.xyz).to(dev)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        r.upload(xyz_dev, ls.offsets)
+    vrt.set_option(r.h, vrt.OPT_STAGE_TIMING, 1)
+    c = vrt.camera_c(cam)
+    p = vrt.params_c(alpha=wl["alpha"], ao_cones=wl["ao"], cull=wl["cull"])
+    rgba = torch.empty((cam.height, cam.width, 4), dtype=torch.float32, device=dev)
+    fid = torch.empty((cam.height, cam.width), dtype=torch.int32, device=dev)
+    ft = torch.empty((cam.height, cam.width), dtype=torch.float32, device=dev)
+    rgba_host = torch.empty_like(rgba, device="cpu").pin_memory()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def frame(f, host=False):
+        first, blk = (upd_host if host else upd_dev)[f % n_upd]
+        vrt.update_vertices(r.h, first, blk)
+        vrt.voxelize(r.h)
+        vrt.build_mips(r.h)
+        vrt.cull(r.h, c, p)
+        vrt.trace(r.h, c, p, rgba, fid, ft)
+
+    with torch.cuda.stream(stream):
+        for f in range(args.warmup):
+            frame(f)
+        vrt.sync(r.h)
+    st0 = vrt.get_stats(r.h)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage_ms = {k: [] for k in vrt.STAGES}
+    barrier()
+    wall0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk, torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)            # evict L2 between frames (outside the events)
+            ev[i][0].record(stream)
+            frame(args.warmup + i)
+            ev[i][1].record(stream)
+            for k, v in vrt.get_stage_ms(r.h).items():   # waits for the frame
+                stage_ms[k].append(v)
+        vrt.sync(r.h)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    st = vrt.get_stats(r.h)
+    frame_ms = [a.elapsed_time(b) for a, b in ev]
+    mean_ms = statistics.mean(frame_ms)
+    launches = (st["kernel_launches"] - st0["kernel_launches"])
+
+    # ---- end-to-end through the C ABI with host buffers
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            frame(args.warmup + i, host=True)
+            rgba_host.copy_(rgba, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        vrt.sync(r.h)
+    h2d = int(upd_host[0][1].numel() * 4)
+    d2h = int(rgba.numel() * 4)
+
+    # ---- max over ranks
+    vals = torch.tensor([mean_ms, statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    mean_ms, e2e_mean = float(vals[0]), float(vals[1])
+
+    if rank != 0:
+        r.close()
+        return None
+    stages = {k: statistics.mean(v) for k, v in stage_ms.items() if v}
+    dom = max(stages, key=stages.get)
+    peak, peak_src = hbm_peak()
+    px = cam.width * cam.height
+    B = stage_bytes(dom, ls.n, ls.n_vertices, st, px)
+    achieved = B / (stages[dom] * 1e-3) / 1e9
+    frame_B = sum(stage_bytes(k, ls.n, ls.n_vertices, st, px) for k in stages)
+    srt = sorted(frame_ms)
+    out = {
+        "metric": METRIC,
+        "value": round(mean_ms / world, 4),
+        "unit": "ms/frame",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(mean_ms, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "impl": "ours",
+        "config": {"workload": wl["desc"], "l2": "flushed between frames (512 MB write)",
+                   "segments": ls.n_segments, "grid": ls.n, "pixels": px,
+                   "p50_ms": round(srt[len(srt) // 2], 4),
+                   "p99_ms": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4),
+                   "wall_s": round(wall, 3),
+                   "value_definition": "mean device time per frame (max over ranks) / ranks"},
+        "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "counters": {k: st[k] for k in ("fragments", "fragments_listed", "occupied_voxels",
+                                        "visible_voxels", "repaired_voxels", "exact_decisions",
+                                        "max_count")},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "traffic": None,
+                     "frame_algorithmic_bytes": frame_B,
+                     "frame_frac": round(frame_B / (mean_ms * 1e-3) / 1e9 / peak, 4)},
+        "e2e": {"value": round(e2e_mean, 4), "unit": "ms/frame", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    r.close()
+    if not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = cpu_baseline(wl)
+        except Exception as e:  # the baseline is reported, never required
+            out["cpu_baseline"] = {"value": None, "error": str(e)}
+    return out
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    """The oracle, as it stands, on the host cores; each step is a bounded
+    sample of the workload scaled to ms/frame."""
+    if rank != 0:
+        return None
+    wl = make_workload(args.workload)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, budget_s=4.0)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    return {"metric": METRIC, "value": round(v, 3), "unit": "ms/frame", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["desc"]},
+            "cpu_baseline": {"value": round(v, 3), "unit": "ms/frame", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": round(v, 3), "unit": "ms/frame", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

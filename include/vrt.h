@@ -1,0 +1,209 @@
+/*
+ * vrt.h -- C ABI of the GB300 (sm_103a) voxel ray-tracing library for dynamic
+ * line sets, after Kraaijeveld, Jalba, Vilanova & Chamberland, "Real-Time
+ * Rendering of Dynamic Line Sets using Voxel Ray Tracing" (arXiv 2510.09081).
+ *
+ * The problem (Sec. 3, overview): a set of polylines (no branches, no loops)
+ * with one uniform tube radius, and a camera, go in; an image of the tubes with
+ * optional ambient occlusion and ground-truth transparency comes out. Every
+ * acceleration structure is rebuilt each frame, so the vertices may change
+ * arbitrarily between frames. One frame is
+ *
+ *   vrt_update_vertices (optional) -> vrt_voxelize -> vrt_build_mips (for AO)
+ *     -> vrt_cull -> vrt_trace
+ *
+ * Conventions shared by every call:
+ *  - Units: world coordinates are in voxels; the grid is [0, n)^3 and voxel
+ *    (x, y, z) is the closed box [x, x+1] x [y, y+1] x [z, z+1]. Coordinates are
+ *    snapped to multiples of 2^-14 voxel on ingest and must lie in [-256, 768).
+ *  - Segment i joins vertex i to vertex i+1 of the same polyline (Sec. 3.3);
+ *    segment ids in lists and outputs are these vertex indices.
+ *  - Ordering: every call is asynchronous on the stream given at creation,
+ *    except vrt_sync, vrt_get_stats and the vrt_read_* calls, which wait.
+ *  - Ownership: the library owns all of its device buffers (grid words, list
+ *    offsets, lists, pyramids, scratch). The caller owns its input and output
+ *    buffers; inputs are copied, so the caller may reuse an input buffer once
+ *    the call's stream work has completed.
+ *  - Errors: a call returns VRT_OK or an error code at once for problems the
+ *    host can see (null pointers, bad sizes, host coordinates out of range,
+ *    calls out of order). Problems only the device sees (device coordinates out
+ *    of range, a 16-bit field or the list capacity overflowing, a bounded wait
+ *    giving up) set a per-grid device status word that vrt_sync returns.
+ *    vrt_last_error gives a message for the last error of a grid.
+ *  - Threading: a grid is used from one host thread at a time; distinct grids
+ *    are independent.
+ */
+#ifndef VRT_H
+#define VRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vrt_grid_s* vrt_grid;
+
+typedef enum {
+  VRT_OK = 0,
+  VRT_ERR_INVALID_ARG = 1, /* bad argument or coordinate out of range */
+  VRT_ERR_OOM = 2,         /* device allocation failed */
+  VRT_ERR_OVERFLOW = 3,    /* a 16-bit voxel field or the list capacity overflowed */
+  VRT_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  VRT_ERR_TIMEOUT = 5,     /* a bounded device wait or repair loop gave up */
+  VRT_ERR_STATE = 6,       /* call out of order (e.g. trace before cull) */
+  VRT_ERR_BOUNDS = 7       /* an index left its buffer (checked builds) */
+} vrt_status;
+
+/* Grid description (Sec. 3.1). */
+typedef struct {
+  int32_t n;              /* grid side: power of two in [16, 512] */
+  float radius;           /* tube radius in voxels, (0, 4]; snapped to 2^-14 */
+  float r_min;            /* PWAA radius clamp of Alg. 3; <= 0 selects 0.5 */
+  int32_t occ_scale;      /* occupancy codes per unit occupancy in the packed
+                             word; 0 selects 32 */
+  uint64_t max_fragments; /* list capacity in entries (all voxels); 0 selects
+                             4 (2 rl + 2)^2 (2 rl + 3), at least 24, entries
+                             per uploaded vertex, rl = radius + 2^-9 */
+} vrt_grid_desc;
+
+/* Pinhole or orthographic camera. Basis: f = normalize(target - eye),
+ * right = normalize(f x up), true up = right x f. Pixel (x, y), row 0 at the
+ * top, is sampled at its centre (x + 0.5, y + 0.5).
+ *  perspective: origin eye, direction normalize(f + sx right + sy up') with
+ *    sx = (2 (x+0.5)/W - 1) tan(fovy/2) W/H, sy = (1 - 2 (y+0.5)/H) tan(fovy/2)
+ *  orthographic: direction f, origin eye + ((x+0.5)/W - 0.5) ortho_h W/H right
+ *    + (0.5 - (y+0.5)/H) ortho_h up'. */
+typedef struct {
+  int32_t width, height, ortho;
+  float eye[3], target[3], up[3];
+  float fovy_deg; /* perspective vertical field of view, degrees */
+  float ortho_h;  /* orthographic view height, voxels */
+} vrt_camera;
+
+/* Rendering parameters (Sec. 3.2, 3.4, 3.5). */
+typedef struct {
+  float alpha;      /* opacity of every tube in (0, 1]; 1 = opaque */
+  int32_t ao_cones; /* 0: no ambient occlusion; 6: six cones per hit */
+  int32_t cull;     /* 0: lists for every voxel (voxelize-scan-voxelize);
+                       1: lists for camera-visible voxels only
+                       (voxelize-cull-scan-voxelize) */
+  int32_t k;        /* k-buffer size: 0 picks from alpha; else 1, 8, 16 or 32 */
+} vrt_render_params;
+
+typedef struct {
+  uint64_t fragments;        /* F: (segment, voxel) pairs of the last voxelize */
+  uint64_t fragments_listed; /* entries written to the lists by the last frame */
+  uint64_t sum_occupancy;    /* sum of occupancy codes of the last voxelize */
+  uint64_t exact_decisions;  /* list decisions taken by the exact integer path */
+  uint32_t occupied_voxels;  /* voxels with count > 0 */
+  uint32_t visible_voxels;   /* voxels given lists by the last cull */
+  uint32_t repaired_voxels;  /* culled voxels a ray needed, listed by repair */
+  uint32_t repair_rounds;    /* repair rounds that found work */
+  uint32_t max_count;        /* largest per-voxel count */
+  uint32_t status_bits;      /* raw device status word */
+  uint64_t kernel_launches;  /* kernels launched by this grid since creation */
+} vrt_stats;
+
+/* Create a grid (Sec. 3.1). `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream). On success *out receives the handle; on failure *out is
+ * NULL. Allocates the per-voxel words, offsets and bitmaps (about 9 bytes per
+ * voxel). */
+vrt_status vrt_create_grid(const vrt_grid_desc* desc, void* cuda_stream, vrt_grid* out);
+
+/* Set the polyline topology and the vertices. `xyz`: n_vertices rows of
+ * `stride` floats (stride 3 or 4; the 4th is ignored), host memory if
+ * on_device == 0, else device memory. `polyline_offsets`: HOST array of
+ * n_polylines + 1 non-decreasing int64, first 0 and last n_vertices; polyline
+ * p owns vertices [offsets[p], offsets[p+1]). Copies everything; (re)allocates
+ * the vertex buffers and, when max_fragments was 0, the list capacity. Host
+ * coordinates outside [-256, 768) or not finite give VRT_ERR_INVALID_ARG. */
+vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int64_t n_vertices,
+                               const int64_t* polyline_offsets, int64_t n_polylines,
+                               int32_t on_device);
+
+/* Overwrite vertices [first_vertex, first_vertex + n_vertices) with new
+ * coordinates (same topology); a dynamic frame's update. Same layout and
+ * memory rules as vrt_upload_segments. */
+vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_vertices,
+                               const float* xyz, int32_t stride, int32_t on_device);
+
+/* Ingest (snap, flags, clip normals) and voxelization pass 1 (Sec. 3.1, Alg. 1
+ * walk, Alg. 3 occupancy): for every segment and every voxel within the list
+ * radius of it (r + 2^-9, decided exactly), one 32-bit atomic add of
+ * (occupancy code << 16) | 1 into the voxel's packed word. */
+vrt_status vrt_voxelize(vrt_grid g);
+
+/* Averaging occupancy pyramid (Sec. 3.1): level 0 = min(1, occupancy code sum /
+ * occ_scale), level l+1 = mean of 8 children, down to 1^3. Needs vrt_voxelize. */
+vrt_status vrt_build_mips(vrt_grid g);
+
+/* Culling and list build (Sec. 3.2, 3.3): with p->cull = 1, mark voxels whose
+ * centre sees the camera through the eroded occupancy; exclusive scan of the
+ * counts of marked voxels into list offsets; voxelization pass 2 writes segment
+ * ids into the lists of marked voxels. With p->cull = 0 every occupied voxel is
+ * marked. Needs vrt_voxelize. */
+vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p);
+
+/* Ray tracing (Sec. 3.5): one ray per pixel through the grid by 3D-DDA; in
+ * each voxel every listed segment's first entry into its capsule is tested,
+ * kept if it lies in the voxel and the clip planes keep it; opaque: nearest
+ * hit; transparent: all hits composited front to back in (depth, id) order
+ * through a k-buffer until transmittance < 1e-4. A ray that meets a culled
+ * voxel holding segments has that voxel listed and is traced again, so the
+ * image never depends on culling. Outputs are DEVICE buffers of width*height
+ * entries, row-major from the top row: rgba_out float4 premultiplied (colour =
+ * |unit tangent| * AO, alpha = 1 - transmittance), first_id_out the nearest
+ * accepted segment id or -1 (nullable), first_t_out its depth or +inf
+ * (nullable). Needs vrt_cull (and vrt_build_mips when p->ao_cones > 0). */
+vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p,
+                     float* rgba_out, int32_t* first_id_out, float* first_t_out);
+
+/* Wait for the grid's stream; return the device status (VRT_OK or the first
+ * device-detected error) and clear it. */
+vrt_status vrt_sync(vrt_grid g);
+
+/* Counters of the last frame (waits). */
+vrt_status vrt_get_stats(vrt_grid g, vrt_stats* out);
+
+/* Test readback (waits): packed words in canonical order (x fastest, then y,
+ * then z), n^3 entries. */
+vrt_status vrt_read_grid(vrt_grid g, uint32_t* words_host);
+
+/* Test readback (waits): for each voxel in canonical order its list start and
+ * length (0 when the voxel has no list), and the list storage itself
+ * (*n_ids entries, at most `cap` copied). Entry order within a list is
+ * unspecified. */
+vrt_status vrt_read_lists(vrt_grid g, uint32_t* start_host, uint32_t* len_host, uint32_t* ids_host,
+                          uint64_t cap, uint64_t* n_ids);
+
+/* Test readback (waits): all pyramid levels, level 0 first, each canonical. */
+vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
+
+/* Options. VRT_OPT_FORCE_EXACT (1): value 1 decides every list membership on
+ * the exact integer path instead of the fp32 filter (for testing).
+ * VRT_OPT_STAGE_TIMING (2): value 1 records CUDA events on the grid's stream
+ * around each stage (see vrt_get_stage_ms). */
+#define VRT_OPT_FORCE_EXACT 1
+#define VRT_OPT_STAGE_TIMING 2
+vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value);
+
+/* Stage durations of the last frame in milliseconds (waits), measured with
+ * CUDA events on the grid's stream while VRT_OPT_STAGE_TIMING is on. Order:
+ * 0 ingest, 1 voxelize pass 1, 2 mips, 3 cull marks, 4 scan, 5 voxelize
+ * pass 2, 6 trace, 7 repair rounds (list + re-trace). Stages that did not run
+ * since the last vrt_voxelize read -1. Writes min(n, 8) entries. */
+#define VRT_N_STAGES 8
+vrt_status vrt_get_stage_ms(vrt_grid g, float* ms, int32_t n);
+
+/* Message for the last error of `g` (or of the last failed create when g is
+ * NULL). Valid until the next call on the grid. */
+const char* vrt_last_error(vrt_grid g);
+
+/* Wait for the stream, free every device buffer and the handle. */
+vrt_status vrt_destroy(vrt_grid g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VRT_H */

@@ -1,0 +1,301 @@
+"""GB300 (sm_103a) voxel ray tracing of dynamic line sets.
+
+Python binding of ``libvrt.so`` (C ABI: ``include/vrt.h``), after Kraaijeveld et
+al., "Real-Time Rendering of Dynamic Line Sets using Voxel Ray Tracing" (arXiv
+2510.09081). The functions carry the names of the C entry points and only
+marshal arguments: every step of a frame (ingest, voxelization, mips, culling,
+scan, list scatter, ray tracing) runs in the library's CUDA kernels. Device
+buffers are torch CUDA tensors; there is no CPU fallback -- without the built
+library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvrt.so")
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_OVERFLOW, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_BOUNDS = range(8)
+STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "OVERFLOW", "CUDA", "TIMEOUT", "STATE", "BOUNDS"]
+OPT_FORCE_EXACT = 1
+OPT_STAGE_TIMING = 2
+STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
+
+# Exported symbols of the C ABI (include/vrt.h)
+SYMBOLS = ["vrt_create_grid", "vrt_upload_segments", "vrt_update_vertices", "vrt_voxelize",
+           "vrt_build_mips", "vrt_cull", "vrt_trace", "vrt_sync", "vrt_get_stats",
+           "vrt_read_grid", "vrt_read_lists", "vrt_read_mips", "vrt_set_option",
+           "vrt_get_stage_ms", "vrt_last_error", "vrt_destroy"]
+
+
+class VrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("radius", ctypes.c_float), ("r_min", ctypes.c_float),
+                ("occ_scale", ctypes.c_int32), ("max_fragments", ctypes.c_uint64)]
+
+
+class CameraC(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("ortho", ctypes.c_int32),
+                ("eye", ctypes.c_float * 3), ("target", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("fovy_deg", ctypes.c_float),
+                ("ortho_h", ctypes.c_float)]
+
+
+class RenderParamsC(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("ao_cones", ctypes.c_int32), ("cull", ctypes.c_int32),
+                ("k", ctypes.c_int32)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("fragments", ctypes.c_uint64), ("fragments_listed", ctypes.c_uint64),
+                ("sum_occupancy", ctypes.c_uint64), ("exact_decisions", ctypes.c_uint64),
+                ("occupied_voxels", ctypes.c_uint32), ("visible_voxels", ctypes.c_uint32),
+                ("repaired_voxels", ctypes.c_uint32), ("repair_rounds", ctypes.c_uint32),
+                ("max_count", ctypes.c_uint32), ("status_bits", ctypes.c_uint32),
+                ("kernel_launches", ctypes.c_uint64)]
+
+
+def load():
+    """Load libvrt.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise VrtError(ERR_STATE, f"{LIB_PATH} is not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "vrt_create_grid": [ctypes.POINTER(GridDesc), P, ctypes.POINTER(P)],
+        "vrt_upload_segments": [P, P, i32, i64, P, i64, i32],
+        "vrt_update_vertices": [P, i64, i64, P, i32, i32],
+        "vrt_voxelize": [P],
+        "vrt_build_mips": [P],
+        "vrt_cull": [P, ctypes.POINTER(CameraC), ctypes.POINTER(RenderParamsC)],
+        "vrt_trace": [P, ctypes.POINTER(CameraC), ctypes.POINTER(RenderParamsC), P, P, P],
+        "vrt_sync": [P],
+        "vrt_get_stats": [P, ctypes.POINTER(StatsC)],
+        "vrt_read_grid": [P, P],
+        "vrt_read_lists": [P, P, P, P, u64, ctypes.POINTER(u64)],
+        "vrt_read_mips": [P, P, u64],
+        "vrt_set_option": [P, i32, i64],
+        "vrt_get_stage_ms": [P, P, i32],
+        "vrt_destroy": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.vrt_last_error.argtypes = [P]
+    lib.vrt_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status, g=None):
+    if status != OK:
+        msg = load().vrt_last_error(g)
+        raise VrtError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _is_device(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def camera_c(cam) -> CameraC:
+    c = CameraC()
+    c.width, c.height, c.ortho = int(cam.width), int(cam.height), int(cam.ortho)
+    c.eye[:] = [float(v) for v in cam.eye]
+    c.target[:] = [float(v) for v in cam.target]
+    c.up[:] = [float(v) for v in cam.up]
+    c.fovy_deg = float(getattr(cam, "fovy_deg", 45.0))
+    c.ortho_h = float(getattr(cam, "ortho_h", 0.0))
+    return c
+
+
+def params_c(alpha=1.0, ao_cones=0, cull=0, k=0) -> RenderParamsC:
+    return RenderParamsC(alpha=float(alpha), ao_cones=int(ao_cones), cull=int(cull), k=int(k))
+
+
+# ------------------------------------------------------------ C entry points
+def create_grid(n, radius, r_min=0.5, occ_scale=32, max_fragments=0, stream=None):
+    lib = load()
+    d = GridDesc(n=int(n), radius=float(radius), r_min=float(r_min), occ_scale=int(occ_scale),
+                 max_fragments=int(max_fragments))
+    h = ctypes.c_void_p()
+    _check(lib.vrt_create_grid(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def upload_segments(g, xyz, offsets):
+    """xyz: float32 [V, 3|4] numpy array (host) or torch CUDA tensor (device);
+    offsets: int64 [P + 1] (host)."""
+    off = np.ascontiguousarray(np.asarray(offsets), dtype=np.int64)
+    dev = _is_device(xyz)
+    if not dev:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    else:
+        assert xyz.is_contiguous() and str(xyz.dtype) == "torch.float32"
+    V = int(xyz.shape[0])
+    stride = int(xyz.shape[1]) if V else 3
+    _check(load().vrt_upload_segments(g, _ptr(xyz), stride, V, off.ctypes.data, off.shape[0] - 1,
+                                      int(dev)), g)
+
+
+def update_vertices(g, first_vertex, xyz):
+    dev = _is_device(xyz)
+    if not dev:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    V = int(xyz.shape[0])
+    stride = int(xyz.shape[1]) if V else 3
+    _check(load().vrt_update_vertices(g, int(first_vertex), V, _ptr(xyz), stride, int(dev)), g)
+
+
+def voxelize(g):
+    _check(load().vrt_voxelize(g), g)
+
+
+def build_mips(g):
+    _check(load().vrt_build_mips(g), g)
+
+
+def cull(g, cam, params):
+    c = cam if isinstance(cam, CameraC) else camera_c(cam)
+    _check(load().vrt_cull(g, ctypes.byref(c), ctypes.byref(params)), g)
+
+
+def trace(g, cam, params, rgba, first_id=None, first_t=None):
+    """rgba: torch float32 CUDA tensor [H, W, 4]; first_id int32 [H, W];
+    first_t float32 [H, W] (both optional)."""
+    c = cam if isinstance(cam, CameraC) else camera_c(cam)
+    _check(load().vrt_trace(g, ctypes.byref(c), ctypes.byref(params), _ptr(rgba), _ptr(first_id),
+                            _ptr(first_t)), g)
+
+
+def sync(g):
+    _check(load().vrt_sync(g), g)
+
+
+def get_stats(g) -> dict:
+    s = StatsC()
+    _check(load().vrt_get_stats(g, ctypes.byref(s)), g)
+    return {k: int(getattr(s, k)) for k, _ in StatsC._fields_}
+
+
+def read_grid(g, n):
+    out = np.zeros(n ** 3, np.uint32)
+    _check(load().vrt_read_grid(g, out.ctypes.data), g)
+    return out
+
+
+def read_lists(g, n, cap=None):
+    start = np.zeros(n ** 3, np.uint32)
+    ln = np.zeros(n ** 3, np.uint32)
+    tot = ctypes.c_uint64(0)
+    _check(load().vrt_read_lists(g, start.ctypes.data, ln.ctypes.data, None, 0, ctypes.byref(tot)), g)
+    ids = np.zeros(max(int(tot.value), 1), np.uint32)
+    _check(load().vrt_read_lists(g, start.ctypes.data, ln.ctypes.data, ids.ctypes.data,
+                                 ids.shape[0], ctypes.byref(tot)), g)
+    return start, ln, ids[:int(tot.value)]
+
+
+def read_mips(g, n):
+    sizes, m = [], n
+    while m >= 1:
+        sizes.append(m)
+        m //= 2
+    tot = sum(s ** 3 for s in sizes)
+    out = np.zeros(tot, np.float32)
+    _check(load().vrt_read_mips(g, out.ctypes.data, tot), g)
+    levels, o = [], 0
+    for s in sizes:
+        levels.append(out[o:o + s ** 3].reshape(s, s, s))
+        o += s ** 3
+    return levels
+
+
+def set_option(g, option, value):
+    _check(load().vrt_set_option(g, int(option), int(value)), g)
+
+
+def get_stage_ms(g) -> dict:
+    ms = np.zeros(len(STAGES), np.float32)
+    _check(load().vrt_get_stage_ms(g, ms.ctypes.data, len(STAGES)), g)
+    return {k: float(v) for k, v in zip(STAGES, ms) if v >= 0}
+
+
+def destroy(g):
+    if g:
+        _check(load().vrt_destroy(g))
+
+
+# --------------------------------------------------------------- convenience
+class Renderer:
+    """One line set on one grid, with torch output buffers; ``frame`` runs
+    voxelize -> (mips) -> cull -> trace on the device."""
+
+    def __init__(self, n, radius, r_min=0.5, occ_scale=32, max_fragments=0, stream=None):
+        self.n = int(n)
+        self.h = create_grid(n, radius, r_min, occ_scale, max_fragments, stream)
+        self._bufs = None
+
+    def close(self):
+        if self.h:
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, xyz, offsets):
+        upload_segments(self.h, xyz, offsets)
+
+    def update(self, first_vertex, xyz):
+        update_vertices(self.h, first_vertex, xyz)
+
+    def buffers(self, width, height):
+        import torch
+        if self._bufs is None or self._bufs[0].shape[:2] != (height, width):
+            self._bufs = (torch.empty((height, width, 4), dtype=torch.float32, device="cuda"),
+                          torch.empty((height, width), dtype=torch.int32, device="cuda"),
+                          torch.empty((height, width), dtype=torch.float32, device="cuda"))
+        return self._bufs
+
+    def frame(self, cam, alpha=1.0, ao_cones=0, cull_on=0, k=0, voxelize_first=True):
+        p = params_c(alpha, ao_cones, cull_on, k)
+        c = camera_c(cam)
+        rgba, fid, ft = self.buffers(c.width, c.height)
+        if voxelize_first:
+            voxelize(self.h)
+            if ao_cones:
+                build_mips(self.h)
+        cull(self.h, c, p)
+        trace(self.h, c, p, rgba, fid, ft)
+        return rgba, fid, ft

@@ -1,0 +1,621 @@
+// C ABI of libvrt (include/vrt.h): handle, device memory, stream ordering and
+// status. Every step of the frame runs in the kernels of this library; this
+// file only validates arguments, allocates, and issues launches and copies on
+// the grid's stream.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "vrt.h"
+
+using namespace vrt;
+
+struct vrt_grid_s {
+  int n = 0, log2n = 0, log2nb = 0;
+  float r = 0, r_min = 0.5f;
+  int R = 0, RL = 0;
+  int occ_scale = 32;
+  uint64_t max_frag_desc = 0;
+  cudaStream_t stream = nullptr;
+  // vertices
+  long long V = 0, P = 0, V_alloc = 0;
+  float* raw = nullptr;
+  uint8_t* flags = nullptr;
+  float4* pos = nullptr;
+  float4* nrm = nullptr;
+  // voxels
+  uint32_t *word = nullptr, *cur = nullptr, *vis = nullptr, *visb = nullptr, *occb = nullptr;
+  uint32_t *need = nullptr, *needb = nullptr;
+  uint8_t* eroded = nullptr;
+  uint32_t* lists = nullptr;
+  unsigned long long list_cap = 0;
+  unsigned long long* tile_state = nullptr;
+  uint32_t n_tiles = 0;
+  float* mips = nullptr;
+  long long lev_off[11] = {0};
+  int n_levels = 0;
+  uint32_t* vq[2] = {nullptr, nullptr};
+  uint32_t vq_cap = 0;
+  uint32_t* pq[2] = {nullptr, nullptr};
+  uint32_t pq_cap = 0;
+  DevStatus* st = nullptr;
+  int force_exact = 0;
+  // stage timing
+  unsigned long long launches = 0;  // kernels launched by this grid
+  bool timing = false;
+  cudaEvent_t ev[VRT_N_STAGES][2] = {};
+  bool ev_used[VRT_N_STAGES] = {};
+  // frame state
+  int stage = 0;  // 0 created, 1 vertices set, 2 voxelized, 3 lists built
+  bool mips_valid = false;
+  int culled = 0;
+  std::string err;
+};
+
+static std::string g_create_error;
+
+namespace {
+
+vrt_status fail(vrt_grid g, vrt_status s, const std::string& msg) {
+  if (g) g->err = msg; else g_create_error = msg;
+  return s;
+}
+
+vrt_status cuda_fail(vrt_grid g, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(g, e == cudaErrorMemoryAllocation ? VRT_ERR_OOM : VRT_ERR_CUDA, m);
+}
+
+#define VRT_CUDA(g, call)                              \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(g, e_, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+GridDev gdev(vrt_grid g) {
+  GridDev d;
+  d.n = g->n; d.log2n = g->log2n; d.log2nb = g->log2nb;
+  d.r = g->r;
+  d.rl = (float)(g->RL) / kUnits;
+  d.R = g->R; d.RL = g->RL;
+  d.r_clamp = fmaxf(g->r, g->r_min);
+  d.corr = (g->r / d.r_clamp) * (g->r / d.r_clamp);
+  d.occ_scale = (float)g->occ_scale;
+  d.force_exact = g->force_exact;
+  d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.visb = g->visb; d.occb = g->occb;
+  d.lists = g->lists; d.list_cap = g->list_cap;
+  d.st = g->st;
+  return d;
+}
+
+bool host_coords_ok(const float* xyz, int stride, long long V) {
+  for (long long i = 0; i < V; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const float x = xyz[i * stride + k];
+      if (!(x >= kCoordMin && x < kCoordMax)) return false;
+    }
+  return true;
+}
+
+vrt_status copy_vertices(vrt_grid g, long long first, long long V, const float* xyz, int stride,
+                         int on_device) {
+  if (V == 0) return VRT_OK;
+  VRT_CUDA(g, cudaMemcpy2DAsync(g->raw + 3 * first, 3 * sizeof(float), xyz,
+                                (size_t)stride * sizeof(float), 3 * sizeof(float), (size_t)V,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                g->stream));
+  return VRT_OK;
+}
+
+void make_camdev(const HostCamera& c, CamDev& cd) {
+  auto sub = [](const double* a, const double* b, double* o) { for (int k = 0; k < 3; ++k) o[k] = a[k] - b[k]; };
+  auto nrm = [](double* v) { double l = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); for (int k = 0; k < 3; ++k) v[k] /= l; };
+  auto crs = [](const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1]; o[1] = a[2] * b[0] - a[0] * b[2]; o[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  double f[3], rt[3], up[3];
+  sub(c.target, c.eye, f); nrm(f);
+  crs(f, c.up, rt); nrm(rt);
+  crs(rt, f, up);
+  const double W = c.width, H = c.height;
+  auto F3 = [](double x, double y, double z) { return make_float3((float)x, (float)y, (float)z); };
+  cd.width = c.width; cd.height = c.height; cd.ortho = c.ortho;
+  if (c.ortho) {
+    const double oh = c.ortho_h, ow = oh * W / H;
+    double o0[3], ox[3], oy[3];
+    for (int k = 0; k < 3; ++k) {
+      o0[k] = c.eye[k] - 0.5 * ow * rt[k] + 0.5 * oh * up[k];
+      ox[k] = ow / W * rt[k];
+      oy[k] = -oh / H * up[k];
+    }
+    cd.o0 = F3(o0[0], o0[1], o0[2]); cd.ox = F3(ox[0], ox[1], ox[2]); cd.oy = F3(oy[0], oy[1], oy[2]);
+    cd.d0 = F3(f[0], f[1], f[2]);
+    cd.dx = cd.dy = make_float3(0.f, 0.f, 0.f);
+  } else {
+    const double th = std::tan(c.fovy_deg * 3.14159265358979323846 / 360.0);
+    const double as = W / H;
+    double d0[3], dx[3], dy[3];
+    for (int k = 0; k < 3; ++k) {
+      d0[k] = f[k] - th * as * rt[k] + th * up[k];
+      dx[k] = 2.0 * th * as / W * rt[k];
+      dy[k] = -2.0 * th / H * up[k];
+    }
+    cd.o0 = F3(c.eye[0], c.eye[1], c.eye[2]);
+    cd.ox = cd.oy = make_float3(0.f, 0.f, 0.f);
+    cd.d0 = F3(d0[0], d0[1], d0[2]); cd.dx = F3(dx[0], dx[1], dx[2]); cd.dy = F3(dy[0], dy[1], dy[2]);
+  }
+}
+
+bool camera_ok(const vrt_camera* c) {
+  if (!c || c->width <= 0 || c->height <= 0) return false;
+  if ((long long)c->width * c->height >= (1ll << 31)) return false;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->eye[k]) || !std::isfinite(c->target[k]) || !std::isfinite(c->up[k])) return false;
+  double f[3], up[3] = {c->up[0], c->up[1], c->up[2]};
+  for (int k = 0; k < 3; ++k) f[k] = (double)c->target[k] - c->eye[k];
+  const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  if (!(fl > 0)) return false;
+  const double cx = f[1] * up[2] - f[2] * up[1], cy = f[2] * up[0] - f[0] * up[2], cz = f[0] * up[1] - f[1] * up[0];
+  if (!(cx * cx + cy * cy + cz * cz > 0)) return false;
+  if (c->ortho) return c->ortho_h > 0;
+  return c->fovy_deg > 0 && c->fovy_deg < 180;
+}
+
+HostCamera host_cam(const vrt_camera* c) {
+  HostCamera h;
+  h.width = c->width; h.height = c->height; h.ortho = c->ortho;
+  for (int k = 0; k < 3; ++k) { h.eye[k] = c->eye[k]; h.target[k] = c->target[k]; h.up[k] = c->up[k]; }
+  h.fovy_deg = c->fovy_deg; h.ortho_h = c->ortho_h;
+  return h;
+}
+
+enum { ST_INGEST, ST_PASS1, ST_MIPS, ST_CULL, ST_SCAN, ST_PASS2, ST_TRACE, ST_REPAIR };
+
+void stage_mark(vrt_grid g, int stage, int end) {
+  if (!g->timing) return;
+  cudaEventRecord(g->ev[stage][end], g->stream);
+  if (end) g->ev_used[stage] = true;
+}
+
+void free_all(vrt_grid g) {
+  for (int i = 0; i < VRT_N_STAGES; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
+  dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
+  dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->visb); dfree(g->occb);
+  dfree(g->need); dfree(g->needb); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
+  dfree(g->mips); dfree(g->vq[0]); dfree(g->vq[1]); dfree(g->pq[0]); dfree(g->pq[1]);
+  dfree(g->st);
+}
+
+}  // namespace
+
+extern "C" {
+
+vrt_status vrt_create_grid(const vrt_grid_desc* desc, void* cuda_stream, vrt_grid* out) {
+  if (!out) return fail(nullptr, VRT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(nullptr, VRT_ERR_INVALID_ARG, "desc is NULL");
+  const int n = desc->n;
+  if (n < 16 || n > 512 || (n & (n - 1)))
+    return fail(nullptr, VRT_ERR_INVALID_ARG, "grid side must be a power of two in [16, 512]");
+  if (!(desc->radius > 0.0f) || desc->radius > 4.0f)
+    return fail(nullptr, VRT_ERR_INVALID_ARG, "radius must be in (0, 4]");
+  if (desc->occ_scale < 0 || desc->occ_scale > 65535)
+    return fail(nullptr, VRT_ERR_INVALID_ARG, "occ_scale must be in [0, 65535]");
+  vrt_grid g = new (std::nothrow) vrt_grid_s();
+  if (!g) return fail(nullptr, VRT_ERR_OOM, "host allocation failed");
+  g->n = n;
+  while ((1 << g->log2n) < n) ++g->log2n;
+  g->log2nb = g->log2n - 2;
+  g->R = (int)std::nearbyint((double)desc->radius * 16384.0);
+  g->RL = g->R + kListMarginUnits;
+  g->r = (float)g->R / kUnits;
+  g->r_min = desc->r_min > 0 ? desc->r_min : 0.5f;
+  g->occ_scale = desc->occ_scale > 0 ? desc->occ_scale : 32;
+  g->max_frag_desc = desc->max_fragments;
+  g->stream = (cudaStream_t)cuda_stream;
+  const size_t nv = (size_t)n * n * n;
+  const size_t nb = nv / 64;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chk(dalloc(&g->word, nv));
+  chk(dalloc(&g->cur, nv));
+  chk(dalloc(&g->vis, nv / 32));
+  chk(dalloc(&g->need, nv / 32));
+  chk(dalloc(&g->visb, (nb + 31) / 32));
+  chk(dalloc(&g->occb, (nb + 31) / 32));
+  chk(dalloc(&g->needb, (nb + 31) / 32));
+  g->n_tiles = (uint32_t)(nv / 4096);
+  chk(dalloc(&g->tile_state, g->n_tiles));
+  chk(dalloc(&g->st, 1));
+  g->vq_cap = (uint32_t)nv;  // a voxel enters the repair queue at most once per list build
+  chk(dalloc(&g->vq[0], g->vq_cap));
+  chk(dalloc(&g->vq[1], g->vq_cap));
+  if (e == cudaSuccess) chk(cudaMemsetAsync(g->st, 0, sizeof(DevStatus), g->stream));
+  if (e == cudaSuccess) chk(cudaMemsetAsync(g->word, 0, nv * 4, g->stream));
+  if (e == cudaSuccess) chk(cudaMemsetAsync(g->need, 0, nv / 8, g->stream));
+  if (e != cudaSuccess) {
+    vrt_status s = cuda_fail(nullptr, e, "vrt_create_grid");
+    free_all(g);
+    delete g;
+    return s;
+  }
+  // pyramid offsets
+  long long off = 0, m = n;
+  g->n_levels = 0;
+  while (m >= 1) {
+    g->lev_off[g->n_levels++] = off;
+    off += m * m * m;
+    m >>= 1;
+  }
+  *out = g;
+  return VRT_OK;
+}
+
+vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int64_t n_vertices,
+                               const int64_t* offsets, int64_t n_polylines, int32_t on_device) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (stride != 3 && stride != 4) return fail(g, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  if (n_vertices < 0 || n_polylines < 0 || n_vertices >= (1ll << 31))
+    return fail(g, VRT_ERR_INVALID_ARG, "bad vertex or polyline count");
+  if (n_vertices > 0 && !xyz) return fail(g, VRT_ERR_INVALID_ARG, "xyz is NULL");
+  if (!offsets) return fail(g, VRT_ERR_INVALID_ARG, "polyline_offsets is NULL");
+  if (offsets[0] != 0 || offsets[n_polylines] != n_vertices)
+    return fail(g, VRT_ERR_INVALID_ARG, "offsets must start at 0 and end at n_vertices");
+  std::vector<uint8_t> fl((size_t)n_vertices, 0);
+  for (long long p = 0; p < n_polylines; ++p) {
+    if (offsets[p + 1] < offsets[p]) return fail(g, VRT_ERR_INVALID_ARG, "offsets must not decrease");
+    if (offsets[p + 1] > offsets[p]) {
+      fl[offsets[p]] |= kFirst;
+      fl[offsets[p + 1] - 1] |= kLast;
+    }
+  }
+  if (!on_device && !host_coords_ok(xyz, stride, n_vertices))
+    return fail(g, VRT_ERR_INVALID_ARG, "coordinates must be finite and in [-256, 768)");
+  const long long V = n_vertices;
+  if (V > g->V_alloc) {
+    VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+    dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
+    g->V_alloc = 0;
+    VRT_CUDA(g, dalloc(&g->raw, 3 * (size_t)V + 6));
+    VRT_CUDA(g, dalloc(&g->flags, (size_t)V));
+    VRT_CUDA(g, dalloc(&g->pos, (size_t)V + 1));
+    VRT_CUDA(g, dalloc(&g->nrm, (size_t)V + 1));
+    g->V_alloc = V;
+  }
+  // default capacity: a generous bound on fragments per segment for tubes of
+  // this radius, (2 rl + 2)^2 (2 rl + 3) * 4, at least 24
+  const double rl = (double)g->RL / 16384.0;
+  const double per = std::max(24.0, 4.0 * (2 * rl + 2) * (2 * rl + 2) * (2 * rl + 3));
+  unsigned long long cap = g->max_frag_desc ? g->max_frag_desc
+                                            : (unsigned long long)(per * (double)std::max(V, 1ll));
+  cap = std::min<unsigned long long>(cap, 0xffffffffull);
+  if (cap != g->list_cap || !g->lists) {
+    VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+    dfree(g->lists);
+    g->list_cap = 0;
+    VRT_CUDA(g, dalloc(&g->lists, (size_t)cap));
+    g->list_cap = cap;
+  }
+  g->V = V;
+  g->P = n_polylines;
+  if (V > 0) {
+    VRT_CUDA(g, cudaMemcpyAsync(g->flags, fl.data(), (size_t)V, cudaMemcpyHostToDevice, g->stream));
+    vrt_status s = copy_vertices(g, 0, V, xyz, stride, on_device);
+    if (s != VRT_OK) return s;
+    VRT_CUDA(g, cudaStreamSynchronize(g->stream));  // fl is a host temporary
+  }
+  g->stage = 1;
+  g->mips_valid = false;
+  return VRT_OK;
+}
+
+vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_vertices,
+                               const float* xyz, int32_t stride, int32_t on_device) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (g->stage < 1) return fail(g, VRT_ERR_STATE, "vrt_upload_segments first");
+  if (stride != 3 && stride != 4) return fail(g, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  if (first_vertex < 0 || n_vertices < 0 || first_vertex + n_vertices > g->V)
+    return fail(g, VRT_ERR_INVALID_ARG, "vertex range outside the uploaded set");
+  if (n_vertices > 0 && !xyz) return fail(g, VRT_ERR_INVALID_ARG, "xyz is NULL");
+  if (!on_device && !host_coords_ok(xyz, stride, n_vertices))
+    return fail(g, VRT_ERR_INVALID_ARG, "coordinates must be finite and in [-256, 768)");
+  vrt_status s = copy_vertices(g, first_vertex, n_vertices, xyz, stride, on_device);
+  if (s != VRT_OK) return s;
+  g->stage = 1;
+  g->mips_valid = false;
+  return VRT_OK;
+}
+
+vrt_status vrt_voxelize(vrt_grid g) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (g->stage < 1) return fail(g, VRT_ERR_STATE, "vrt_upload_segments first");
+  const size_t nv = (size_t)g->n * g->n * g->n;
+  // clear the counters (everything after the error word)
+  VRT_CUDA(g, cudaMemsetAsync((char*)g->st + sizeof(unsigned int), 0,
+                              sizeof(DevStatus) - sizeof(unsigned int), g->stream));
+  VRT_CUDA(g, cudaMemsetAsync(g->word, 0, nv * 4, g->stream));
+  for (int i = 0; i < VRT_N_STAGES; ++i) g->ev_used[i] = false;
+  stage_mark(g, ST_INGEST, 0);
+  g->launches += launch_ingest(g->raw, g->flags, g->V, g->pos, g->nrm, g->st, g->stream);
+  stage_mark(g, ST_INGEST, 1);
+  stage_mark(g, ST_PASS1, 0);
+  g->launches += launch_pass1(g->pos, g->nrm, g->V, gdev(g), g->stream);
+  stage_mark(g, ST_PASS1, 1);
+  VRT_CUDA(g, cudaGetLastError());
+  g->stage = 2;
+  g->mips_valid = false;
+  return VRT_OK;
+}
+
+vrt_status vrt_build_mips(vrt_grid g) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (g->stage < 2) return fail(g, VRT_ERR_STATE, "vrt_voxelize first");
+  if (!g->mips) VRT_CUDA(g, dalloc(&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  stage_mark(g, ST_MIPS, 0);
+  g->launches += launch_mips(gdev(g), g->mips, g->lev_off, g->n_levels, g->stream);
+  stage_mark(g, ST_MIPS, 1);
+  VRT_CUDA(g, cudaGetLastError());
+  g->mips_valid = true;
+  return VRT_OK;
+}
+
+vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (!p) return fail(g, VRT_ERR_INVALID_ARG, "params is NULL");
+  if (g->stage < 2) return fail(g, VRT_ERR_STATE, "vrt_voxelize first");
+  if (p->cull && !camera_ok(cam)) return fail(g, VRT_ERR_INVALID_ARG, "bad camera");
+  if (p->cull && !(p->alpha > 0.0f && p->alpha <= 1.0f))
+    return fail(g, VRT_ERR_INVALID_ARG, "alpha must be in (0, 1]");
+  const size_t nv = (size_t)g->n * g->n * g->n;
+  const size_t nbw = (nv / 64 + 31) / 32;
+  const GridDev d = gdev(g);
+  // reset the list-build counters (scan tile counter .. end)
+  const size_t off = offsetof(DevStatus, sum_count_field);
+  VRT_CUDA(g, cudaMemsetAsync((char*)g->st + off, 0, sizeof(DevStatus) - off, g->stream));
+  VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, occupied_voxels), 0, sizeof(unsigned int), g->stream));
+  VRT_CUDA(g, cudaMemsetAsync(g->tile_state, 0, (size_t)g->n_tiles * 8, g->stream));
+  stage_mark(g, ST_CULL, 0);
+  if (p->cull) {
+    if (!g->eroded) VRT_CUDA(g, dalloc(&g->eroded, nv));
+    VRT_CUDA(g, cudaMemsetAsync(g->visb, 0, nbw * 4, g->stream));
+    g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->stream);
+  } else {
+    VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
+    VRT_CUDA(g, cudaMemsetAsync(g->visb, 0xff, nbw * 4, g->stream));
+  }
+  stage_mark(g, ST_CULL, 1);
+  stage_mark(g, ST_SCAN, 0);
+  g->launches += launch_scan(d, p->cull ? 0 : 1, g->tile_state, g->n_tiles, g->stream);
+  g->launches += launch_finalize(d, g->stream);
+  stage_mark(g, ST_SCAN, 1);
+  stage_mark(g, ST_PASS2, 0);
+  g->launches += launch_pass2(g->pos, g->V, d, p->cull ? 1 : 0, nullptr, nullptr, nullptr, g->stream);
+  stage_mark(g, ST_PASS2, 1);
+  VRT_CUDA(g, cudaGetLastError());
+  g->culled = p->cull ? 1 : 0;
+  g->stage = 3;
+  return VRT_OK;
+}
+
+vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p, float* rgba,
+                     int32_t* first_id, float* first_t) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (!p || !rgba) return fail(g, VRT_ERR_INVALID_ARG, "params or rgba_out is NULL");
+  if (!camera_ok(cam)) return fail(g, VRT_ERR_INVALID_ARG, "bad camera");
+  if (!(p->alpha > 0.0f && p->alpha <= 1.0f)) return fail(g, VRT_ERR_INVALID_ARG, "alpha must be in (0, 1]");
+  if (p->ao_cones != 0 && p->ao_cones != 6) return fail(g, VRT_ERR_INVALID_ARG, "ao_cones must be 0 or 6");
+  if (p->k != 0 && p->k != 1 && p->k != 8 && p->k != 16 && p->k != 32)
+    return fail(g, VRT_ERR_INVALID_ARG, "k must be 0, 1, 8, 16 or 32");
+  if (g->stage < 3) return fail(g, VRT_ERR_STATE, "vrt_cull first");
+  if (p->ao_cones && !g->mips_valid) return fail(g, VRT_ERR_STATE, "vrt_build_mips first (ambient occlusion)");
+  int K;
+  if (p->alpha >= 1.0f) {
+    K = 1;
+  } else if (p->k > 1) {
+    K = p->k;
+  } else {
+    const double need = std::ceil(std::log(1e-4) / std::log(1.0 - (double)p->alpha));
+    K = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
+  }
+  const uint32_t npx = (uint32_t)cam->width * (uint32_t)cam->height;
+  if (g->culled && npx > g->pq_cap) {
+    VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+    dfree(g->pq[0]); dfree(g->pq[1]);
+    g->pq_cap = 0;
+    VRT_CUDA(g, dalloc(&g->pq[0], npx));
+    VRT_CUDA(g, dalloc(&g->pq[1], npx));
+    g->pq_cap = npx;
+  }
+  TraceArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = gdev(g);
+  make_camdev(host_cam(cam), a.cam);
+  a.pos = g->pos; a.nrm = g->nrm;
+  a.n_vert = (uint32_t)g->V;
+  a.alpha = p->alpha; a.ao = p->ao_cones ? 1 : 0;
+  a.mips = g->mips;
+  for (int l = 0; l < 11; ++l) a.lev_off[l] = g->lev_off[l];
+  a.n_levels = g->n_levels;
+  a.rgba = reinterpret_cast<float4*>(rgba);
+  a.first_id = first_id;
+  a.first_t = first_t;
+  a.need = g->need;
+  a.vq_cap = g->vq_cap;
+  a.pq_cap = g->pq_cap;
+  a.vq = g->vq[0]; a.vq_cnt = &g->st->vq_cnt[0];
+  a.pq = g->pq[0]; a.pq_cnt = &g->st->pq_cnt[0];
+  // Traces before the next-to-last repair round stop after a few queued
+  // voxels (cheap, may need another round); the re-trace of the next-to-last
+  // round queues without limit, so the last round always completes.
+  a.max_queue = kMaxRepairRounds >= 2 ? kRayQueueLimit : 0xffffffffu;
+  VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, vq_cnt), 0,
+                              4 * sizeof(unsigned int), g->stream));
+  stage_mark(g, ST_TRACE, 0);
+  g->launches += launch_trace(a, K, g->stream);
+  stage_mark(g, ST_TRACE, 1);
+  if (g->culled) {
+    stage_mark(g, ST_REPAIR, 0);
+    const GridDev d = gdev(g);
+    const size_t nbw = ((size_t)g->n * g->n * g->n / 64 + 31) / 32;
+    for (int r = 0; r < kMaxRepairRounds; ++r) {
+      const int ci = r & 1, nx = ci ^ 1;
+      VRT_CUDA(g, cudaMemsetAsync(g->needb, 0, nbw * 4, g->stream));
+      g->launches += launch_repair_alloc(d, g->needb, g->vq[ci], &g->st->vq_cnt[ci], g->vq_cap, g->stream);
+      g->launches += launch_pass2(g->pos, g->V, d, 2, g->need, g->needb, &g->st->vq_cnt[ci], g->stream);
+      g->launches += launch_repair_clear(d, g->need, g->vq[ci], &g->st->vq_cnt[ci], g->vq_cap, nx, g->stream);
+      TraceArgs b = a;
+      b.pix_list = g->pq[ci];
+      b.pix_count = &g->st->pq_cnt[ci];
+      b.vq = g->vq[nx]; b.vq_cnt = &g->st->vq_cnt[nx];
+      b.pq = g->pq[nx]; b.pq_cnt = &g->st->pq_cnt[nx];
+      b.max_queue = (r + 2 >= kMaxRepairRounds) ? 0xffffffffu : kRayQueueLimit;
+      g->launches += launch_trace(b, K, g->stream);
+    }
+    stage_mark(g, ST_REPAIR, 1);
+  }
+  VRT_CUDA(g, cudaGetLastError());
+  return VRT_OK;
+}
+
+vrt_status vrt_sync(vrt_grid g) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  DevStatus hs;
+  VRT_CUDA(g, cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost));
+  uint32_t e = hs.err;
+  if (g->culled && hs.vq_cnt[kMaxRepairRounds & 1] != 0) e |= kErrRepair;
+  if (hs.err) VRT_CUDA(g, cudaMemset(g->st, 0, sizeof(unsigned int)));
+  if (e & kErrRange) return fail(g, VRT_ERR_INVALID_ARG, "device coordinates out of range or not finite");
+  if (e & kErrOverflow) return fail(g, VRT_ERR_OVERFLOW, "a 16-bit voxel field or the list capacity overflowed");
+  if (e & kErrTimeout) return fail(g, VRT_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (e & kErrRepair) return fail(g, VRT_ERR_TIMEOUT, "culling repair did not converge");
+  if (e & kErrBounds) return fail(g, VRT_ERR_BOUNDS, "index out of bounds");
+  return VRT_OK;
+}
+
+vrt_status vrt_get_stats(vrt_grid g, vrt_stats* out) {
+  if (!g || !out) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  DevStatus hs;
+  VRT_CUDA(g, cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost));
+  out->fragments = hs.F;
+  out->fragments_listed = hs.listed;
+  out->sum_occupancy = hs.sum_q;
+  out->exact_decisions = hs.exact_decisions;
+  out->occupied_voxels = hs.occupied_voxels;
+  out->visible_voxels = hs.visible_voxels;
+  out->repaired_voxels = hs.repaired_voxels;
+  out->repair_rounds = hs.repair_rounds;
+  out->max_count = hs.max_count;
+  out->status_bits = hs.err;
+  out->kernel_launches = g->launches;
+  return VRT_OK;
+}
+
+vrt_status vrt_read_grid(vrt_grid g, uint32_t* words) {
+  if (!g || !words) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  const int n = g->n;
+  const size_t nv = (size_t)n * n * n;
+  std::vector<uint32_t> w(nv);
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  VRT_CUDA(g, cudaMemcpy(w.data(), g->word, nv * 4, cudaMemcpyDeviceToHost));
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) words[((size_t)z * n + y) * n + x] = w[brick_index(x, y, z, g->log2nb)];
+  return VRT_OK;
+}
+
+vrt_status vrt_read_lists(vrt_grid g, uint32_t* start, uint32_t* len, uint32_t* ids, uint64_t cap,
+                          uint64_t* n_ids) {
+  if (!g || !start || !len) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  if (g->stage < 3) return fail(g, VRT_ERR_STATE, "vrt_cull first");
+  const int n = g->n;
+  const size_t nv = (size_t)n * n * n;
+  std::vector<uint32_t> w(nv), c(nv), vis(nv / 32);
+  DevStatus hs;
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  VRT_CUDA(g, cudaMemcpy(w.data(), g->word, nv * 4, cudaMemcpyDeviceToHost));
+  VRT_CUDA(g, cudaMemcpy(c.data(), g->cur, nv * 4, cudaMemcpyDeviceToHost));
+  VRT_CUDA(g, cudaMemcpy(vis.data(), g->vis, nv / 8, cudaMemcpyDeviceToHost));
+  VRT_CUDA(g, cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost));
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        const uint32_t i = brick_index(x, y, z, g->log2nb);
+        const size_t o = ((size_t)z * n + y) * n + x;
+        const uint32_t cnt = w[i] & 0xffffu;
+        if (cnt && ((vis[i >> 5] >> (i & 31)) & 1u)) { start[o] = c[i] - cnt; len[o] = cnt; }
+        else { start[o] = 0; len[o] = 0; }
+      }
+  const uint64_t tot = std::min<uint64_t>(hs.list_tail, g->list_cap);
+  if (n_ids) *n_ids = tot;
+  if (ids && tot) VRT_CUDA(g, cudaMemcpy(ids, g->lists, std::min(tot, cap) * 4, cudaMemcpyDeviceToHost));
+  return VRT_OK;
+}
+
+vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats) {
+  if (!g || !host) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  if (!g->mips_valid) return fail(g, VRT_ERR_STATE, "vrt_build_mips first");
+  const uint64_t tot = (uint64_t)g->lev_off[g->n_levels - 1] + 1;
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  VRT_CUDA(g, cudaMemcpy(host, g->mips, std::min(tot, n_floats) * 4, cudaMemcpyDeviceToHost));
+  return VRT_OK;
+}
+
+vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (option == VRT_OPT_FORCE_EXACT) {
+    g->force_exact = value ? 1 : 0;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_STAGE_TIMING) {
+    if (value && !g->ev[0][0])
+      for (int i = 0; i < VRT_N_STAGES; ++i)
+        for (int j = 0; j < 2; ++j) VRT_CUDA(g, cudaEventCreate(&g->ev[i][j]));
+    g->timing = value != 0;
+    return VRT_OK;
+  }
+  return fail(g, VRT_ERR_INVALID_ARG, "unknown option");
+}
+
+vrt_status vrt_get_stage_ms(vrt_grid g, float* ms, int32_t n) {
+  if (!g || !ms || n < 0) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  for (int i = 0; i < n && i < VRT_N_STAGES; ++i) {
+    ms[i] = -1.0f;
+    if (g->timing && g->ev_used[i]) VRT_CUDA(g, cudaEventElapsedTime(&ms[i], g->ev[i][0], g->ev[i][1]));
+  }
+  return VRT_OK;
+}
+
+const char* vrt_last_error(vrt_grid g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+vrt_status vrt_destroy(vrt_grid g) {
+  if (!g) return VRT_OK;
+  cudaStreamSynchronize(g->stream);
+  free_all(g);
+  delete g;
+  return VRT_OK;
+}
+
+}  // extern "C"

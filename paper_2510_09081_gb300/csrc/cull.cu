@@ -1,0 +1,187 @@
+// A3: voxel-based view culling (Sec. 3.2).
+//
+// Occupancy is eroded by taking the minimum over each voxel and its six
+// neighbours (outside the grid counts as empty), which makes the estimate of
+// what blocks the view conservative. Every occupied voxel inside the view
+// frustum then marches from its centre toward the camera through the eroded
+// occupancy. The march turns occupancy into optical depth: tubes of radius r
+// filling a volume fraction e are crossed 2 e / (pi r) times per unit length,
+// and each crossing lets 1 - alpha through (an opaque crossing counts as one
+// unit), so depth += kappa * e * (path length in the voxel) with
+// kappa = 2 / (pi r) * (-ln(1 - alpha) or 1). A voxel is marked visible unless
+// the depth in front of it exceeds ln(1e4) + 3, past the depth where a ray
+// stops. The marks decide which voxels get lists; voxels a ray later needs but
+// that were left unmarked are listed by the trace's repair rounds, so the
+// marks only affect speed.
+// A brick bit is set when any voxel of the brick is marked (segment culling
+// in pass 2 tests the segment's box against these bits).
+#include <cmath>
+
+#include "launch.h"
+
+namespace vrt {
+
+constexpr float kCullDepth = 9.2103404f + 3.0f;  // ln(1e4) + 3
+
+__device__ __forceinline__ void brick_coords(uint32_t idx, int log2nb, int& x, int& y, int& z) {
+  const uint32_t b = idx >> 6, l = idx & 63u;
+  const uint32_t mask = (1u << log2nb) - 1u;
+  x = (int)(((b & mask) << 2) | (l & 3u));
+  y = (int)((((b >> log2nb) & mask) << 2) | ((l >> 2) & 3u));
+  z = (int)(((b >> (2 * log2nb)) << 2) | (l >> 4));
+}
+
+__device__ __forceinline__ uint32_t occ8(const GridDev& g, int x, int y, int z) {
+  if ((unsigned)x >= (unsigned)g.n || (unsigned)y >= (unsigned)g.n || (unsigned)z >= (unsigned)g.n)
+    return 0u;
+  const uint32_t q = __ldg(&g.word[brick_index(x, y, z, g.log2nb)]) >> 16;
+  return min(255u, (uint32_t)((float)q * (255.0f / g.occ_scale)));
+}
+
+__global__ void __launch_bounds__(256) k_erode(GridDev g, uint8_t* __restrict__ eroded) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (uint32_t)g.n * g.n * g.n) return;
+  int x, y, z;
+  brick_coords(idx, g.log2nb, x, y, z);
+  uint32_t e = occ8(g, x, y, z);
+  if (e) {
+    e = min(e, occ8(g, x - 1, y, z));
+    e = min(e, occ8(g, x + 1, y, z));
+    e = min(e, occ8(g, x, y - 1, z));
+    e = min(e, occ8(g, x, y + 1, z));
+    e = min(e, occ8(g, x, y, z - 1));
+    e = min(e, occ8(g, x, y, z + 1));
+  }
+  eroded[idx] = (uint8_t)e;
+}
+
+struct CullCam {
+  float3 eye, f, nr, nl, nt, nb;  // perspective: inward side-plane normals
+  float3 rt, up;                  // orthographic: half extents along right / up
+  float hw, hh, lr, ll, lt, lb;   // |n| * sqrt(3)/2 margins
+  float kappa;                    // optical depth per unit length at full occupancy
+  int ortho;
+};
+
+__global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
+                                                 const uint8_t* __restrict__ eroded) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
+  bool visible = false;
+  if (idx < nvox && (__ldg(&g.word[idx]) & 0xffffu)) {
+    int x, y, z;
+    brick_coords(idx, g.log2nb, x, y, z);
+    const float3 c = make_float3(x + 0.5f, y + 0.5f, z + 0.5f);
+    const float3 v = c - cc.eye;
+    const float h = 0.8660254f;
+    bool inside;
+    float3 dir;
+    float tmax;
+    if (cc.ortho) {
+      inside = dot3(v, cc.f) >= -h && fabsf(dot3(v, cc.rt)) <= cc.hw + h &&
+               fabsf(dot3(v, cc.up)) <= cc.hh + h;
+      dir = make_float3(-cc.f.x, -cc.f.y, -cc.f.z);
+      tmax = __int_as_float(0x7f800000);
+    } else {
+      inside = dot3(v, cc.f) >= -h && dot3(v, cc.nr) >= -cc.lr && dot3(v, cc.nl) >= -cc.ll &&
+               dot3(v, cc.nt) >= -cc.lt && dot3(v, cc.nb) >= -cc.lb;
+      const float dist = sqrtf(dot3(v, v));
+      dir = dist > 0.0f ? (-1.0f / dist) * v : make_float3(0.f, 0.f, 1.f);
+      tmax = dist;
+    }
+    if (inside) {
+      // march voxel by voxel from the centre toward the camera
+      const int n = g.n;
+      int p[3] = {x, y, z};
+      int step[3];
+      float inv[3], og[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float dk = cmp3(dir, k);
+        og[k] = cmp3(c, k);
+        step[k] = dk > 0.0f ? 1 : (dk < 0.0f ? -1 : 0);
+        inv[k] = dk != 0.0f ? 1.0f / dk : 0.0f;
+      }
+      float depth = 0.0f, tprev = 0.0f;
+      visible = true;
+      for (int it = 0; it < 3 * n; ++it) {
+        float te = __int_as_float(0x7f800000);
+        int ke = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (step[k] == 0) continue;
+          const float tk = ((float)(step[k] > 0 ? p[k] + 1 : p[k]) - og[k]) * inv[k];
+          if (tk < te) { te = tk; ke = k; }
+        }
+        if (te >= tmax) break;
+        p[ke] += step[ke];
+        if (p[ke] < 0 || p[ke] >= n) break;
+        float tn = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (step[k] == 0) continue;
+          tn = fminf(tn, ((float)(step[k] > 0 ? p[k] + 1 : p[k]) - og[k]) * inv[k]);
+        }
+        tn = fminf(tn, tmax);
+        const float e = (float)__ldg(&eroded[brick_index(p[0], p[1], p[2], g.log2nb)]) *
+                        (1.0f / 255.0f);
+        depth = fmaf(cc.kappa * e, tn - te, depth);
+        tprev = te;
+        if (depth > kCullDepth) { visible = false; break; }
+      }
+      (void)tprev;
+    }
+  }
+  const uint32_t m = __ballot_sync(0xffffffffu, visible);
+  if ((threadIdx.x & 31) == 0 && idx < nvox) {
+    g.vis[idx >> 5] = m;
+    if (m) atomicOr(&g.visb[idx >> 11], 1u << ((idx >> 6) & 31));
+  }
+}
+
+namespace {
+struct D3 { double x, y, z; };
+D3 sub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+D3 add(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+D3 mul(double s, D3 a) { return {s * a.x, s * a.y, s * a.z}; }
+D3 crs(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+double len(D3 a) { return std::sqrt(a.x * a.x + a.y * a.y + a.z * a.z); }
+D3 nrmz(D3 a) { return mul(1.0 / len(a), a); }
+float3 tof(D3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
+}  // namespace
+
+int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
+                cudaStream_t s) {
+  const D3 eye = {cam.eye[0], cam.eye[1], cam.eye[2]};
+  const D3 tgt = {cam.target[0], cam.target[1], cam.target[2]};
+  const D3 upw = {cam.up[0], cam.up[1], cam.up[2]};
+  const D3 f = nrmz(sub(tgt, eye));
+  const D3 rt = nrmz(crs(f, upw));
+  const D3 up = crs(rt, f);
+  const double aspect = (double)cam.width / (double)cam.height;
+  const double h = 0.8660254037844386;
+  CullCam cc;
+  cc.ortho = cam.ortho;
+  cc.kappa = (float)(2.0 / (3.14159265358979323846 * g.r) *
+                     (alpha < 1.0f ? -std::log(1.0 - (double)alpha) : 1.0));
+  cc.eye = tof(eye);
+  cc.f = tof(f);
+  cc.rt = tof(rt);
+  cc.up = tof(up);
+  cc.hh = (float)(0.5 * cam.ortho_h);
+  cc.hw = (float)(0.5 * cam.ortho_h * aspect);
+  const double th = std::tan(cam.fovy_deg * 3.14159265358979323846 / 360.0);
+  const D3 nr = sub(mul(th * aspect, f), rt), nl = add(mul(th * aspect, f), rt);
+  const D3 nt = sub(mul(th, f), up), nb = add(mul(th, f), up);
+  cc.nr = tof(nr); cc.nl = tof(nl); cc.nt = tof(nt); cc.nb = tof(nb);
+  // a little slack on top of the bounding sphere keeps the test conservative
+  cc.lr = (float)(len(nr) * h + 1e-3); cc.ll = (float)(len(nl) * h + 1e-3);
+  cc.lt = (float)(len(nt) * h + 1e-3); cc.lb = (float)(len(nb) * h + 1e-3);
+  const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
+  const int T = 256;
+  k_erode<<<(nvox + T - 1) / T, T, 0, s>>>(g, eroded);
+  k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded);
+  return 2;
+}
+
+}  // namespace vrt

@@ -1,0 +1,52 @@
+// A0 ingest: snap vertices to multiples of 2^-14 voxel, attach polyline flags
+// and compute clip-plane normals as central-difference tangents (Sec. 3.1,
+// clipped capsules after Gross & Gumhold), disabled at polyline ends.
+#include "launch.h"
+
+namespace vrt {
+
+__device__ __forceinline__ float snap(float x, bool& bad) {
+  if (!(x >= kCoordMin && x < kCoordMax)) {  // also catches NaN
+    bad = true;
+    x = fminf(fmaxf(x, kCoordMin), kCoordMax - 1.0f);
+    if (x != x) x = 0.0f;
+  }
+  return rintf(x * kUnits) * (1.0f / kUnits);
+}
+
+__global__ void __launch_bounds__(256) k_ingest(const float* __restrict__ raw,
+                                                const uint8_t* __restrict__ flags, long long V,
+                                                float4* __restrict__ pos, float4* __restrict__ nrm,
+                                                DevStatus* st) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  bool bad = false;
+  const float x = snap(raw[3 * i], bad), y = snap(raw[3 * i + 1], bad), z = snap(raw[3 * i + 2], bad);
+  uint32_t fl = flags[i];
+  float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!(fl & (kFirst | kLast))) {
+    bool b2 = false;
+    const float tx = snap(raw[3 * i + 3], b2) - snap(raw[3 * i - 3], b2);
+    const float ty = snap(raw[3 * i + 4], b2) - snap(raw[3 * i - 2], b2);
+    const float tz = snap(raw[3 * i + 5], b2) - snap(raw[3 * i - 1], b2);
+    const float l2 = tx * tx + ty * ty + tz * tz;
+    if (l2 > 0.0f) {
+      const float l = sqrtf(l2);
+      n = make_float4(tx / l, ty / l, tz / l, 0.f);
+      fl |= kClipOn;
+    }
+  }
+  if (bad) set_err(st, kErrRange);
+  pos[i] = make_float4(x, y, z, __uint_as_float(fl));
+  nrm[i] = n;
+}
+
+int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,
+                   DevStatus* st, cudaStream_t s) {
+  if (V <= 0) return 0;
+  const int T = 256;
+  k_ingest<<<(unsigned)((V + T - 1) / T), T, 0, s>>>(raw, flags, V, pos, nrm, st);
+  return 1;
+}
+
+}  // namespace vrt

@@ -1,0 +1,72 @@
+// Host-side launch wrappers of the libvrt kernels (one translation unit each).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vrt_internal.cuh"
+
+namespace vrt {
+
+// Camera as given through the C ABI, widened to fp64 on the host.
+struct HostCamera {
+  int width, height, ortho;
+  double eye[3], target[3], up[3], fovy_deg, ortho_h;
+};
+
+// Camera in the form the trace kernel consumes (built on the host in fp64).
+struct CamDev {
+  float3 o0, ox, oy;  // origin: o0 (+ (px+.5) ox + (py+.5) oy when orthographic)
+  float3 d0, dx, dy;  // direction: d0 + (px+.5) dx + (py+.5) dy, normalised
+  int width, height, ortho;
+};
+
+struct TraceArgs {
+  GridDev g;
+  CamDev cam;
+  const float4* pos;
+  const float4* nrm;
+  uint32_t n_vert;           // vertices; list entries must be < n_vert - 1
+  float alpha;
+  int ao;
+  const float* mips;
+  long long lev_off[11];
+  int n_levels;
+  float4* rgba;
+  int* first_id;
+  float* first_t;
+  const uint32_t* pix_list;  // trace only these pixels (repair) when non-null
+  const uint32_t* pix_count; // number of entries of pix_list (device)
+  uint32_t* need;            // [n^3 / 32] voxels queued for listing
+  uint32_t* vq;              // out: queued voxels
+  uint32_t* vq_cnt;
+  uint32_t* pq;              // out: pixels to trace again
+  uint32_t* pq_cnt;
+  uint32_t vq_cap, pq_cap;
+  uint32_t max_queue;        // culled voxels one ray may queue before it stops
+};
+
+int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,
+                   DevStatus* st, cudaStream_t s);
+int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,
+                  cudaStream_t s);
+// mode 0: every occupied voxel listed; 1: listed voxels from the cull marks;
+// 2: repair (only voxels whose `need` bit is set, bricks from `needb`)
+int launch_pass2(const float4* pos, long long V, const GridDev& g, int mode, const uint32_t* need,
+                  const uint32_t* needb, const uint32_t* pending, cudaStream_t s);
+int launch_scan(const GridDev& g, int all_visible, unsigned long long* tile_state, uint32_t n_tiles,
+                 cudaStream_t s);
+int launch_finalize(const GridDev& g, cudaStream_t s);
+int launch_mips(const GridDev& g, float* mips, const long long* lev_off, int n_levels,
+                 cudaStream_t s);
+int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
+                cudaStream_t s);
+int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
+// Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
+// them, then clear their `need` bits and the next round's queue counters.
+int launch_repair_alloc(const GridDev& g, uint32_t* needb, const uint32_t* vq,
+                         const uint32_t* vq_cnt, uint32_t vq_cap, cudaStream_t s);
+int launch_repair_clear(const GridDev& g, uint32_t* need, const uint32_t* vq,
+                         const uint32_t* vq_cnt, uint32_t vq_cap, int next, cudaStream_t s);
+
+}  // namespace vrt

@@ -1,0 +1,57 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/vrt.h declares (no GPU needed: nothing here launches work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2510_09081_gb300 as vrt
+from paper_2510_09081_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vrt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vrt_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return vrt.load()
+
+
+def test_header_declares_the_binding_symbols():
+    assert _declared() == sorted(vrt.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_host_side_argument_checks(lib):
+    """Argument errors are reported before any device work."""
+    h = ctypes.c_void_p()
+    bad = vrt.GridDesc(n=100, radius=0.4, r_min=0.5, occ_scale=32, max_fragments=0)
+    assert lib.vrt_create_grid(ctypes.byref(bad), None, ctypes.byref(h)) == vrt.ERR_INVALID_ARG
+    assert b"power of two" in lib.vrt_last_error(None)
+    bad = vrt.GridDesc(n=64, radius=0.0, r_min=0.5, occ_scale=32, max_fragments=0)
+    assert lib.vrt_create_grid(ctypes.byref(bad), None, ctypes.byref(h)) == vrt.ERR_INVALID_ARG
+    assert lib.vrt_create_grid(None, None, ctypes.byref(h)) == vrt.ERR_INVALID_ARG
+    assert lib.vrt_voxelize(None) == vrt.ERR_INVALID_ARG
+    assert lib.vrt_destroy(None) == vrt.OK
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(vrt, "_lib", None)
+    monkeypatch.setattr(vrt, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(vrt.VrtError):
+        vrt.load()
+
+
+def test_build_targets_sm103a_only():
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

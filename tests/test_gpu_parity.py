@@ -1,0 +1,307 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, on seeded
+synthetic line sets that span many bricks, tiles and a ragged image edge.
+Tolerances are stated in tests/parity.py."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2510_09081_gb300 as vrt
+from gen.linesets import (Camera, LineSet, random_polylines, tiny_walks, tiny_walks_camera)
+from parity import RGBA_TOL, check_lists, check_words, compare_image
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def gpu_grid(ls, force_exact=False, occ_scale=32, max_fragments=0):
+    r = vrt.Renderer(ls.n, ls.radius, occ_scale=occ_scale, max_fragments=max_fragments)
+    r.upload(ls.xyz, ls.offsets)
+    if force_exact:
+        vrt.set_option(r.h, vrt.OPT_FORCE_EXACT, 1)
+    return r
+
+
+def gpu_lists(ls, cull=0, cam=None, **kw):
+    r = gpu_grid(ls, **kw)
+    vrt.voxelize(r.h)
+    if cam is None:
+        cam = tiny_walks_camera(ls.n, 16, 16)
+    vrt.cull(r.h, vrt.camera_c(cam), vrt.params_c(cull=cull))
+    vrt.sync(r.h)
+    words = vrt.read_grid(r.h, ls.n)
+    start, ln, ids = vrt.read_lists(r.h, ls.n)
+    st = vrt.get_stats(r.h)
+    r.close()
+    return words, (start, ln, ids), st
+
+
+def gpu_image(r, cam, alpha=1.0, ao=0, cull=0, k=0, voxelize=True):
+    rgba, fid, ft = r.frame(cam, alpha=alpha, ao_cones=ao, cull_on=cull, k=k,
+                            voxelize_first=voxelize)
+    vrt.sync(r.h)
+    return rgba.cpu().numpy(), fid.cpu().numpy(), ft.cpu().numpy()
+
+
+def assert_image(res, max_exempt_frac=0.01):
+    assert res["col_bad"] == 0, res
+    assert res["id_bad"] == 0, res
+    assert res["exempt_colour"] <= max_exempt_frac * res["n"], res
+    assert res["exempt_id"] <= max_exempt_frac * res["n"], res
+    # depth of the first hit: fp32 vs fp64; grazing entries are ill-conditioned
+    assert res["max_t_rel"] < 2e-4, res
+
+
+# ----------------------------------------------------------------- lists
+def test_tiny_walks_words_and_lists():
+    ls = tiny_walks()
+    o = oracle.Oracle.from_lineset(ls)
+    L = o.lists()
+    words, lists, st = gpu_lists(ls)
+    check_words(words, L)
+    check_lists(*lists, L)
+    assert st["fragments"] == L["F"]
+    assert st["fragments_listed"] == L["F"]
+    assert st["status_bits"] == 0
+
+
+def _edge_case_set():
+    """Degenerate segments, one-vertex and empty polylines, lines crossing and
+    running outside the grid, long segments, vertices on voxel faces."""
+    rng = np.random.default_rng(5)
+    pts, offs = [], [0]
+
+    def add(line):
+        line = np.asarray(line, np.float32).reshape(-1, 3)
+        pts.append(line)
+        offs.append(offs[-1] + line.shape[0])
+
+    add([[5, 5, 5], [5, 5, 5], [7, 5, 5]])                 # degenerate first segment
+    add([[10, 10, 10]])                                    # one vertex: no segment
+    add(np.zeros((0, 3)))                                  # empty polyline
+    add([[-3, 8, 8], [12, 9, 7], [35, 10, 9]])             # enters and leaves the grid
+    add([[1, 1, 1], [30, 29, 28]])                          # long diagonal
+    add([[8, 8, 8], [9, 8, 8], [9, 9, 8], [9, 9, 9]])       # on voxel faces / edges
+    add([[20.5, 20.5, 3], [20.5, 20.5, 28]])                # axis-parallel through centres
+    add([[16, 16, 16], [16.0001, 16, 16], [16, 16, 16]])    # tiny zig-zag
+    for _ in range(40):
+        n = int(rng.integers(2, 8))
+        p = rng.uniform(-2, 34, size=3)
+        line = [p]
+        for _ in range(n - 1):
+            p = p + rng.normal(size=3) * rng.uniform(0.0, 6.0)
+            line.append(p)
+        add(np.array(line))
+    xyz = np.concatenate(pts, 0)
+    return LineSet(xyz=xyz, offsets=np.array(offs, np.int64), n=32, radius=0.45)
+
+
+@pytest.mark.parametrize("force_exact", [False, True])
+def test_edge_case_lists(force_exact):
+    ls = _edge_case_set()
+    L = oracle.Oracle.from_lineset(ls).lists()
+    words, lists, st = gpu_lists(ls, force_exact=force_exact)
+    check_words(words, L)
+    check_lists(*lists, L)
+    if force_exact:
+        assert st["exact_decisions"] > st["fragments"]
+
+
+@pytest.mark.parametrize("radius", [0.05, 0.4, 1.3])
+def test_random_polylines_lists(radius):
+    ls = random_polylines(300, (2, 30), 32, radius, seed=int(radius * 100))
+    L = oracle.Oracle.from_lineset(ls).lists()
+    words, lists, _ = gpu_lists(ls)
+    check_words(words, L)
+    check_lists(*lists, L)
+
+
+def test_filter_and_exact_paths_agree_on_ties():
+    """Segments placed exactly at the list radius from voxel faces, edges and
+    corners (on the 2^-14 lattice) exercise the exact fallback."""
+    R = round(0.4 * 16384) + 32
+    u = 1.0 / 16384
+    lines = []
+    for k in range(30):
+        base = np.array([4.0 + k % 5 * 5, 4.0 + (k // 5) * 4, 6.0])
+        off = R * u
+        lines.append([base + [0, -off, 0.5], base + [3, -off, 0.5]])          # face tie
+        d = off / np.sqrt(2)
+        lines.append([base + [-d, -d, -3], base + [-d, -d, 3]])                # near edge
+        lines.append([base + [0.5, 1 + off, 0.2], base + [0.5, 1 + off, 0.8]])  # face tie
+    xyz = np.array(lines, np.float32).reshape(-1, 3)
+    ls = LineSet(xyz=xyz, offsets=np.arange(0, xyz.shape[0] + 1, 2), n=32, radius=0.4)
+    L = oracle.Oracle.from_lineset(ls).lists()
+    w0, l0, st0 = gpu_lists(ls)
+    w1, l1, _ = gpu_lists(ls, force_exact=True)
+    check_lists(*l0, L)
+    check_lists(*l1, L)
+    assert st0["exact_decisions"] > 0
+
+
+# ----------------------------------------------------------------- images
+def _persp_cam(n=64, w=157, h=93):
+    return Camera(width=w, height=h, ortho=0, eye=(n * 1.6, n * 1.3, n * 0.9),
+                  target=(n / 2, n / 2, n / 2), up=(0, 0, 1), fovy_deg=45.0)
+
+
+def test_tiny_walks_opaque_ortho():
+    ls = tiny_walks()
+    o = oracle.Oracle.from_lineset(ls)
+    cam = tiny_walks_camera()
+    ref = o.render(cam, alpha=1.0)
+    r = gpu_grid(ls)
+    res = compare_image(*gpu_image(r, cam), ref)
+    r.close()
+    assert res["hits"] > 50000
+    assert_image(res)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.3, 0.1])
+def test_perspective_images(alpha):
+    ls = tiny_walks(n_lines=600, n_verts=40, seed=123)
+    o = oracle.Oracle.from_lineset(ls)
+    cam = _persp_cam()
+    ref = o.render(cam, alpha=alpha)
+    r = gpu_grid(ls)
+    res = compare_image(*gpu_image(r, cam, alpha=alpha), ref)
+    r.close()
+    assert res["hits"] > 2000
+    assert_image(res)
+
+
+def test_k_buffer_size_does_not_change_the_image():
+    ls = tiny_walks(n_lines=600, n_verts=40, seed=123)
+    cam = _persp_cam()
+    r = gpu_grid(ls)
+    outs = [gpu_image(r, cam, alpha=0.2, k=k) for k in (8, 16, 32)]
+    r.close()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.3])
+def test_culling_never_changes_the_image(alpha):
+    ls = tiny_walks(n_lines=3000, n_verts=60, seed=9)
+    cam = _persp_cam(w=211, h=117)
+    r = gpu_grid(ls)
+    off = gpu_image(r, cam, alpha=alpha, cull=0)
+    on = gpu_image(r, cam, alpha=alpha, cull=1)
+    st = vrt.get_stats(r.h)
+    r.close()
+    for a, b in zip(off, on):
+        assert np.array_equal(a, b)
+    assert st["visible_voxels"] < st["occupied_voxels"]
+
+
+def test_mips_match_oracle():
+    ls = tiny_walks(n_lines=800, n_verts=50, n=64, seed=3)
+    o = oracle.Oracle.from_lineset(ls)
+    L = o.lists()
+    ref = o.mips()
+    r = gpu_grid(ls)
+    vrt.voxelize(r.h)
+    vrt.build_mips(r.h)
+    got = vrt.read_mips(r.h, 64)
+    r.close()
+    # a near-tie occupancy code may differ by one step: bound its effect per level
+    bound = ((L["occ_hi"].astype(np.float64) - L["occ_lo"]) / 32.0).reshape(64, 64, 64)
+    for lvl, (g, f) in enumerate(zip(got, ref)):
+        assert g.shape == f.shape
+        assert np.all(np.abs(g - f) <= bound + 1e-6), lvl
+        m = bound.shape[0] // 2
+        if m >= 1:
+            bound = bound.reshape(m, 2, m, 2, m, 2).mean(axis=(1, 3, 5))
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.4])
+def test_ambient_occlusion_images(alpha):
+    ls = tiny_walks(n_lines=1500, n_verts=60, n=32, radius=0.6, seed=17, start_lo=4.0,
+                    start_hi=28.0)
+    o = oracle.Oracle.from_lineset(ls)
+    cam = Camera(width=96, height=80, ortho=0, eye=(16.0, 16.0, 16.0), target=(40.0, 30.0, 20.0),
+                 up=(0, 0, 1), fovy_deg=60.0)
+    ref = o.render(cam, alpha=alpha, ao_cones=6)
+    r = gpu_grid(ls)
+    res = compare_image(*gpu_image(r, cam, alpha=alpha, ao=6, cull=1), ref)
+    r.close()
+    assert res["hits"] > 1000
+    assert_image(res, max_exempt_frac=0.02)
+
+
+# ------------------------------------------------------------ dynamic data
+def test_update_vertices_equals_fresh_upload():
+    ls = tiny_walks(n_lines=500, n_verts=50, seed=1)
+    ls2 = tiny_walks(n_lines=500, n_verts=50, seed=2)
+    new = ls.xyz.copy()
+    new[5000:9000] = ls2.xyz[5000:9000]
+    r = gpu_grid(ls)
+    vrt.voxelize(r.h)
+    vrt.update_vertices(r.h, 5000, torch.from_numpy(ls2.xyz[5000:9000]).cuda())
+    vrt.voxelize(r.h)
+    vrt.sync(r.h)
+    w_upd = vrt.read_grid(r.h, 64)
+    r.close()
+    fresh = LineSet(xyz=new, offsets=ls.offsets, n=64, radius=ls.radius)
+    L = oracle.Oracle.from_lineset(fresh).lists()
+    check_words(w_upd, L)
+
+
+def test_device_stride4_upload_matches_host():
+    ls = tiny_walks(n_lines=300, n_verts=30, seed=4)
+    x4 = np.concatenate([ls.xyz, np.full((ls.n_vertices, 1), 7.0, np.float32)], 1)
+    r = vrt.Renderer(64, ls.radius)
+    r.upload(torch.from_numpy(x4).cuda(), ls.offsets)
+    vrt.voxelize(r.h)
+    vrt.sync(r.h)
+    w = vrt.read_grid(r.h, 64)
+    r.close()
+    check_words(w, oracle.Oracle.from_lineset(ls).lists())
+
+
+# ------------------------------------------------------------------ errors
+def test_error_reporting():
+    ls = tiny_walks(n_lines=50, n_verts=20, seed=6)
+    bad = ls.xyz.copy()
+    bad[3, 1] = 900.0
+    r = vrt.Renderer(64, 0.4)
+    with pytest.raises(vrt.VrtError) as e:
+        r.upload(bad, ls.offsets)
+    assert e.value.status == vrt.ERR_INVALID_ARG
+    # device input out of range: reported at sync
+    r.upload(torch.from_numpy(bad).cuda(), ls.offsets)
+    vrt.voxelize(r.h)
+    with pytest.raises(vrt.VrtError) as e:
+        vrt.sync(r.h)
+    assert e.value.status == vrt.ERR_INVALID_ARG
+    vrt.sync(r.h)  # cleared
+    # trace before the list build
+    r.upload(ls.xyz, ls.offsets)
+    rgba = torch.zeros((4, 4, 4), device="cuda")
+    with pytest.raises(vrt.VrtError) as e:
+        vrt.trace(r.h, tiny_walks_camera(64, 4, 4), vrt.params_c(), rgba)
+    assert e.value.status == vrt.ERR_STATE
+    r.close()
+
+
+def test_overflow_is_detected():
+    # occupancy field: 2000 coincident segments at scale 65535 wrap 16 bits
+    xyz = np.tile(np.array([[10.5, 10.5, 10.2], [10.5, 10.5, 10.8]], np.float32), (2000, 1))
+    ls = LineSet(xyz=xyz, offsets=np.arange(0, 4001, 2), n=32, radius=0.5)
+    r = gpu_grid(ls, occ_scale=65535)
+    vrt.voxelize(r.h)
+    vrt.cull(r.h, vrt.camera_c(tiny_walks_camera(32, 8, 8)), vrt.params_c())
+    with pytest.raises(vrt.VrtError) as e:
+        vrt.sync(r.h)
+    assert e.value.status == vrt.ERR_OVERFLOW
+    r.close()
+    # list capacity
+    ls = tiny_walks(n_lines=100, n_verts=20, seed=8)
+    r = gpu_grid(ls, max_fragments=1000)
+    vrt.voxelize(r.h)
+    vrt.cull(r.h, vrt.camera_c(tiny_walks_camera(64, 8, 8)), vrt.params_c())
+    with pytest.raises(vrt.VrtError) as e:
+        vrt.sync(r.h)
+    assert e.value.status == vrt.ERR_OVERFLOW
+    r.close()
