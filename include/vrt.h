@@ -196,8 +196,41 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value);
 #define VRT_N_STAGES 8
 vrt_status vrt_get_stage_ms(vrt_grid g, float* ms, int32_t n);
 
-/* Message for the last error of `g` (or of the last failed create when g is
- * NULL). Valid until the next call on the grid. */
+/* Exclusive prefix sum of per-voxel counts that allocates no device memory.
+ * The paper has no counterpart: it is a stand-alone form of the list-offset
+ * scan that vrt_cull runs, for callers that cannot allocate device memory
+ * where they need it -- code whose device memory is owned by a pool or arena,
+ * loops that must not grow or fragment memory mid-frame, real-time paths where
+ * an allocation could block in the driver. Its look-back scratch is a fixed
+ * array inside the library image (about 256 KB), which every GPU that loads
+ * the library holds until the process exits.
+ *   words:      DEVICE, n_voxels packed words; the count is the low 16 bits.
+ *   marks:      DEVICE bitmap (bit i%32 of word i/32 marks voxel i), or NULL
+ *               to count every voxel.
+ *   offsets:    DEVICE output, n_voxels entries: the exclusive prefix sum of
+ *               the counts of marked voxels in the order given.
+ *   n_voxels:   a multiple of 4096, at most 134217728 (512^3); anything else
+ *               returns VRT_ERR_INVALID_ARG before any device work.
+ *   total_out:  DEVICE, one entry (nullable): the sum of the marked counts.
+ *   status_out: DEVICE, one entry (nullable): bit 0 is set (never cleared
+ *               here) if a bounded wait gave up; the offsets are then wrong.
+ * words and offsets must be 16-byte aligned. The grid's own list build
+ * orders voxels in 4^3 bricks (brick index x-fastest, then 16 z + 4 y + x
+ * inside the brick); pass words in that order to reproduce its offsets.
+ * The call issues two cudaMemsetAsync (clearing its scratch) and one kernel
+ * on `cuda_stream`; it calls no cudaMalloc, cudaFree or allocating library
+ * routine. Every call shares the scratch array and leaves its contents
+ * behind; calls that overlap on the GPU (two streams, two threads) race and
+ * give wrong results. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. Errors: VRT_ERR_INVALID_ARG, VRT_ERR_CUDA;
+ * vrt_last_error(NULL) gives the message. */
+vrt_status vrt_scan_counts_noalloc(const uint32_t* words, const uint32_t* marks, uint32_t* offsets,
+                                   uint64_t n_voxels, uint32_t* total_out, uint32_t* status_out,
+                                   void* cuda_stream);
+
+/* Message for the last error of `g` (or, when g is NULL, of the last failed
+ * create or stand-alone call). Valid until the next call on the grid. */
 const char* vrt_last_error(vrt_grid g);
 
 /* Wait for the stream, free every device buffer and the handle. */

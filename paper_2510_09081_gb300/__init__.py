@@ -29,7 +29,7 @@ STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
 SYMBOLS = ["vrt_create_grid", "vrt_upload_segments", "vrt_update_vertices", "vrt_voxelize",
            "vrt_build_mips", "vrt_cull", "vrt_trace", "vrt_sync", "vrt_get_stats",
            "vrt_read_grid", "vrt_read_lists", "vrt_read_mips", "vrt_set_option",
-           "vrt_get_stage_ms", "vrt_last_error", "vrt_destroy"]
+           "vrt_get_stage_ms", "vrt_scan_counts_noalloc", "vrt_last_error", "vrt_destroy"]
 
 
 class VrtError(RuntimeError):
@@ -88,6 +88,7 @@ def load():
         "vrt_read_mips": [P, P, u64],
         "vrt_set_option": [P, i32, i64],
         "vrt_get_stage_ms": [P, P, i32],
+        "vrt_scan_counts_noalloc": [P, P, P, u64, P, P, P],
         "vrt_destroy": [P],
     }
     for name, args in sig.items():
@@ -246,6 +247,15 @@ def get_stage_ms(g) -> dict:
     ms = np.zeros(len(STAGES), np.float32)
     _check(load().vrt_get_stage_ms(g, ms.ctypes.data, len(STAGES)), g)
     return {k: float(v) for k, v in zip(STAGES, ms) if v >= 0}
+
+
+def scan_counts_noalloc(words, offsets, marks=None, total=None, status=None, stream=None,
+                        n_voxels=None):
+    """Exclusive scan of packed-word counts without any device allocation
+    (vrt_scan_counts_noalloc). All arguments are torch CUDA tensors."""
+    n = int(words.numel()) if n_voxels is None else int(n_voxels)
+    _check(load().vrt_scan_counts_noalloc(_ptr(words), _ptr(marks), _ptr(offsets), n,
+                                          _ptr(total), _ptr(status), _stream_ptr(stream)))
 
 
 def destroy(g):

@@ -57,7 +57,7 @@ struct vrt_grid_s {
   std::string err;
 };
 
-static std::string g_create_error;
+std::string g_create_error;  // last error without a grid (creation, stand-alone calls)
 
 namespace {
 
