@@ -40,10 +40,10 @@ def log(*a):
 
 
 # ---------------------------------------------------------------- workloads
-def make_workload(name):
+def make_workload(name, scale=1.0):
     from gen import linesets as G
     if name == "bundles":
-        bs = G.bundles()
+        bs = G.bundles(n_lines=int(round(100_000 * scale)))
         cam = G.bundles_camera()
         upd = lambda f: G.bundles_update(bs, f)  # noqa: E731
         return dict(ls=bs.lineset, cam=cam, update=upd, alpha=0.3, ao=0, cull=1,
@@ -203,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     t0 = time.time()
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.scale)
     ls, cam = wl["ls"], wl["cam"]
     log(f"[bench] workload ready in {time.time() - t0:.1f}s: V={ls.n_vertices} S={ls.n_segments}")
     n_upd = max(1, min(args.steps + args.warmup, 4))
@@ -315,7 +315,8 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic",
         "impl": "ours",
-        "config": {"workload": wl["desc"], "l2": "flushed between frames (512 MB write)",
+        "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else ""),
+                   "l2": "flushed between frames (512 MB write)",
                    "segments": ls.n_segments, "grid": ls.n, "pixels": px,
                    "p50_ms": round(srt[len(srt) // 2], 4),
                    "p99_ms": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4),
@@ -351,7 +352,7 @@ def run_reference(args, rank):
     sample of the workload scaled to ms/frame."""
     if rank != 0:
         return None
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.scale)
     vals = []
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(wl, budget_s=4.0)
@@ -377,6 +378,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="fraction of the bundle streamlines (small cases for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
