@@ -324,8 +324,8 @@ def run_ours(args, rank, world, local_rank):
                    "value_definition": "mean device time per frame (max over ranks) / ranks"},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "counters": {k: st[k] for k in ("fragments", "fragments_listed", "occupied_voxels",
-                                        "visible_voxels", "repaired_voxels", "exact_decisions",
-                                        "max_count")},
+                                        "visible_voxels", "repaired_voxels", "retraced_pixels",
+                                        "exact_decisions", "max_count")},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,

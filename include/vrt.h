@@ -88,7 +88,10 @@ typedef struct {
   int32_t cull;     /* 0: lists for every voxel (voxelize-scan-voxelize);
                        1: lists for camera-visible voxels only
                        (voxelize-cull-scan-voxelize) */
-  int32_t k;        /* k-buffer size: 0 picks from alpha; else 1, 8, 16 or 32 */
+  int32_t k;        /* 0, 1, 8, 16 or 32; kept for compatibility: the trace
+                       keeps 4 nearest keys per lane (128 per warp) and
+                       rescans a list when it must, so the image does not
+                       depend on k */
 } vrt_render_params;
 
 typedef struct {
@@ -103,6 +106,8 @@ typedef struct {
   uint32_t max_count;        /* largest per-voxel count */
   uint32_t status_bits;      /* raw device status word */
   uint64_t kernel_launches;  /* kernels launched by this grid since creation */
+  uint32_t retraced_pixels;  /* pixels traced again by the last frame's repair */
+  uint32_t reserved;
 } vrt_stats;
 
 /* Create a grid (Sec. 3.1). `cuda_stream` is a cudaStream_t (NULL = legacy
@@ -146,10 +151,10 @@ vrt_status vrt_build_mips(vrt_grid g);
 vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p);
 
 /* Ray tracing (Sec. 3.5): one ray per pixel through the grid by 3D-DDA; in
- * each voxel every listed segment's first entry into its capsule is tested,
- * kept if it lies in the voxel and the clip planes keep it; opaque: nearest
- * hit; transparent: all hits composited front to back in (depth, id) order
- * through a k-buffer until transmittance < 1e-4. A ray that meets a culled
+ * each voxel every listed segment's first entry into its capsule is tested
+ * (a warp splits each voxel's list), kept if it lies in the voxel and the clip
+ * planes keep it; opaque: nearest hit; transparent: all hits composited front
+ * to back in (depth, id) order until transmittance < 1e-4. A ray that meets a culled
  * voxel holding segments has that voxel listed and is traced again, so the
  * image never depends on culling. Outputs are DEVICE buffers of width*height
  * entries, row-major from the top row: rgba_out float4 premultiplied (colour =

@@ -61,7 +61,8 @@ class StatsC(ctypes.Structure):
                 ("occupied_voxels", ctypes.c_uint32), ("visible_voxels", ctypes.c_uint32),
                 ("repaired_voxels", ctypes.c_uint32), ("repair_rounds", ctypes.c_uint32),
                 ("max_count", ctypes.c_uint32), ("status_bits", ctypes.c_uint32),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64), ("retraced_pixels", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 def load():

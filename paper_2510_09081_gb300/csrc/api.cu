@@ -34,6 +34,8 @@ struct vrt_grid_s {
   uint8_t* eroded = nullptr;
   uint32_t* lists = nullptr;
   unsigned long long list_cap = 0;
+  uint2* xq = nullptr;      // pairs the fp32 filter left to the exact path
+  uint32_t xq_cap = 0;
   unsigned long long* tile_state = nullptr;
   uint32_t n_tiles = 0;
   float* mips = nullptr;
@@ -102,6 +104,7 @@ GridDev gdev(vrt_grid g) {
   d.force_exact = g->force_exact;
   d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.visb = g->visb; d.occb = g->occb;
   d.lists = g->lists; d.list_cap = g->list_cap;
+  d.xq = g->xq; d.xq_cap = g->xq_cap;
   d.st = g->st;
   return d;
 }
@@ -195,6 +198,23 @@ void stage_mark(vrt_grid g, int stage, int end) {
   if (end) g->ev_used[stage] = true;
 }
 
+// Capacity of the exact-path queue: the fp32 filter leaves about 1% of the
+// candidate voxels undecided; 4 per vertex (at least 4M) covers that with a
+// wide margin. The forced-exact test mode sends every candidate, so it gets
+// the list capacity's worth.
+vrt_status size_exact_queue(vrt_grid g) {
+  unsigned long long want = std::max<unsigned long long>(4ull * (unsigned long long)g->V_alloc, 1ull << 22);
+  if (g->force_exact) want = std::max<unsigned long long>(want, std::min<unsigned long long>(g->list_cap, 1ull << 28));
+  want = std::min<unsigned long long>(want, 0xffffffffull);
+  if (g->xq && g->xq_cap >= want) return VRT_OK;
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  dfree(g->xq);
+  g->xq_cap = 0;
+  VRT_CUDA(g, dalloc(&g->xq, (size_t)want));
+  g->xq_cap = (uint32_t)want;
+  return VRT_OK;
+}
+
 void free_all(vrt_grid g) {
   for (int i = 0; i < VRT_N_STAGES; ++i)
     for (int j = 0; j < 2; ++j)
@@ -202,6 +222,7 @@ void free_all(vrt_grid g) {
   dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
   dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->visb); dfree(g->occb);
   dfree(g->need); dfree(g->needb); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
+  dfree(g->xq);
   dfree(g->mips); dfree(g->vq[0]); dfree(g->vq[1]); dfree(g->pq[0]); dfree(g->pq[1]);
   dfree(g->st);
 }
@@ -315,6 +336,10 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
     g->list_cap = 0;
     VRT_CUDA(g, dalloc(&g->lists, (size_t)cap));
     g->list_cap = cap;
+  }
+  {
+    vrt_status s = size_exact_queue(g);
+    if (s != VRT_OK) return s;
   }
   g->V = V;
   g->P = n_polylines;
@@ -480,7 +505,10 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
     for (int r = 0; r < kMaxRepairRounds; ++r) {
       const int ci = r & 1, nx = ci ^ 1;
       VRT_CUDA(g, cudaMemsetAsync(g->needb, 0, nbw * 4, g->stream));
-      g->launches += launch_repair_alloc(d, g->needb, g->vq[ci], &g->st->vq_cnt[ci], g->vq_cap, g->stream);
+      VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, xq_cnt), 0,
+                                  sizeof(unsigned int), g->stream));
+      g->launches += launch_repair_alloc(d, g->needb, g->vq[ci], &g->st->vq_cnt[ci], &g->st->pq_cnt[ci],
+                                         g->vq_cap, g->stream);
       g->launches += launch_pass2(g->pos, g->V, d, 2, g->need, g->needb, &g->st->vq_cnt[ci], g->stream);
       g->launches += launch_repair_clear(d, g->need, g->vq[ci], &g->st->vq_cnt[ci], g->vq_cap, nx, g->stream);
       TraceArgs b = a;
@@ -529,6 +557,7 @@ vrt_status vrt_get_stats(vrt_grid g, vrt_stats* out) {
   out->max_count = hs.max_count;
   out->status_bits = hs.err;
   out->kernel_launches = g->launches;
+  out->retraced_pixels = hs.retraced_pixels;
   return VRT_OK;
 }
 
@@ -586,7 +615,7 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
   if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
   if (option == VRT_OPT_FORCE_EXACT) {
     g->force_exact = value ? 1 : 0;
-    return VRT_OK;
+    return g->V_alloc ? size_exact_queue(g) : VRT_OK;
   }
   if (option == VRT_OPT_STAGE_TIMING) {
     if (value && !g->ev[0][0])

@@ -8,7 +8,9 @@
 // filling a volume fraction e are crossed 2 e / (pi r) times per unit length,
 // and each crossing lets 1 - alpha through (an opaque crossing counts as one
 // unit), so depth += kappa * e * (path length in the voxel) with
-// kappa = 2 / (pi r) * (-ln(1 - alpha) or 1). A voxel is marked visible unless
+// kappa = 1/2 * 2 / (pi r) * (-ln(1 - alpha) or 1); the factor 1/2 covers the
+// occupancy estimate's excess over the true tube volume (about 4/3 for thin
+// tubes under the PWAA clamp). A voxel is marked visible unless
 // the depth in front of it exceeds ln(1e4) + 3, past the depth where a ray
 // stops. The marks decide which voxels get lists; voxels a ray later needs but
 // that were left unmarked are listed by the trace's repair rounds, so the
@@ -162,7 +164,9 @@ int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* e
   const double h = 0.8660254037844386;
   CullCam cc;
   cc.ortho = cam.ortho;
-  cc.kappa = (float)(2.0 / (3.14159265358979323846 * g.r) *
+  // x 1/2: sampled PWAA occupancy integrates to about 4/3 of the tubes' true
+  // volume, and the estimate must stay below the depth a ray really sees
+  cc.kappa = (float)(0.5 * 2.0 / (3.14159265358979323846 * g.r) *
                      (alpha < 1.0f ? -std::log(1.0 - (double)alpha) : 1.0));
   cc.eye = tof(eye);
   cc.f = tof(f);

@@ -65,7 +65,8 @@ int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
 // Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
 // them, then clear their `need` bits and the next round's queue counters.
 int launch_repair_alloc(const GridDev& g, uint32_t* needb, const uint32_t* vq,
-                         const uint32_t* vq_cnt, uint32_t vq_cap, cudaStream_t s);
+                        const uint32_t* vq_cnt, const uint32_t* pq_cnt, uint32_t vq_cap,
+                        cudaStream_t s);
 int launch_repair_clear(const GridDev& g, uint32_t* need, const uint32_t* vq,
                          const uint32_t* vq_cnt, uint32_t vq_cap, int next, cudaStream_t s);
 

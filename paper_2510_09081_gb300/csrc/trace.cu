@@ -1,21 +1,31 @@
 // A6: voxel ray tracing (Sec. 3.5).
 //
-// One thread per pixel; a warp covers an 8x4 pixel tile so its rays cross
-// the same voxels and lists. Each ray is clipped to the grid box and stepped
-// by 3D-DDA (Amanatides & Woo); bricks with no occupied voxel are crossed in
-// one step (empty-space skipping). In each voxel every listed segment's first
-// entry into its capsule is computed; an entry counts only if it lies in this
-// voxel's parameter interval [t_enter, t_exit) -- the intervals partition the
-// ray, so each hit is counted once and hits come out voxel by voxel in depth
-// order -- and both clip planes keep it.
-//  - opaque (K = 1): nearest entry in the first voxel that has one, then stop;
-//  - transparent (K > 1): the K nearest entries of the voxel are kept sorted
-//    in registers as 64-bit keys (depth bits << 32 | segment id), composited
-//    front to back; a voxel holding more than K entries is scanned again for
-//    keys beyond the last composited one (ground-truth order). The ray stops
-//    once transmittance drops below 1e-4.
-// Shading: colour = |unit tangent| (tangent colouring) times cone-traced
-// ambient occlusion when enabled (six cones over the occupancy pyramid).
+// One ray per pixel; a warp owns an 8x4 pixel tile (in the repair re-trace, 32
+// queued pixels). Each lane steps its own ray by 3D-DDA (Amanatides & Woo)
+// through the grid box, crossing bricks with no occupied voxel in one step
+// (empty-space skipping), until it reaches a voxel with a list. The warp then
+// processes the pending voxels of its lanes one at a time, all 32 lanes
+// splitting that voxel's list (lane l takes entries l, l+32, ...), so a long
+// list costs len/32 steps and no lane idles on another lane's list.
+//
+// For each listed segment the lane computes the first entry of the ray into
+// the segment's capsule; an entry counts only if it lies in the voxel's ray
+// interval [t_enter, t_exit) -- the intervals partition the ray, so each hit
+// is counted once and hits come out voxel by voxel in depth order -- and both
+// clip planes keep it. A cheap line-to-line distance test skips segments whose
+// line passes farther than r from the ray.
+//  - opaque: the warp's minimum 64-bit key (depth bits << 32 | segment id) is
+//    the voxel's nearest hit; the ray stops at the first voxel that has one.
+//  - transparent: each lane keeps its 4 smallest keys beyond the last
+//    composited one; the warp extracts keys in global (depth, id) order by
+//    repeated minimum reductions -- only up to the smallest key a lane had to
+//    drop, beyond which it rescans the list -- shades up to 32 of them in
+//    parallel (one per lane), and accumulates them in key order,
+//    C += T alpha c, T *= 1 - alpha, until T < 1e-4 (ground-truth order).
+// Shading: colour = |unit tangent| per component times cone-traced ambient
+// occlusion when enabled (six cones over the occupancy pyramid; a cone's
+// occlusion is 1 - prod(1 - s_k) over its samples, so the samples of one hit
+// can be taken by different lanes).
 //
 // Culling validation: a ray that reaches a voxel holding segments but no list
 // queues the voxel (deduplicated by a bitmap), marches on as if the voxel were
@@ -29,8 +39,27 @@
 
 namespace vrt {
 
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kLaneKeys = 4;              // transparent: keys kept per lane per scan
+constexpr float kConeTan = 1.1180340f;    // tan(half angle), cos(half angle) = 2/3
+constexpr int kConeSteps = 4;             // samples per cone: t = 1, 2.118, 4.486, 9.502 (<= 16)
+
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, uint32_t i) {
   return (bits[i >> 5] >> (i & 31)) & 1u;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(FULL, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ float3 shfl3(float3 v, int src) {
+  return make_float3(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src),
+                     __shfl_sync(FULL, v.z, src));
 }
 
 // ------------------------------------------------ ambient occlusion (Sec 3.4)
@@ -58,34 +87,60 @@ __device__ __forceinline__ float trilinear(const float* lev, int m, float scale,
   return acc;
 }
 
-__device__ float ambient_occlusion(const TraceArgs& A, float3 P) {
-  const float tan_half = 1.1180340f;  // cos(half angle) = 2/3: six cones tile the sphere
+// One cone sample: cone c (axis c/2, sign by parity), step k; returns 1 - s.
+__device__ float cone_sample_clear(const TraceArgs& A, float3 P, int c, int k) {
+  float t = 1.0f;
+  for (int q = 0; q < k; ++q) t += 0.5f * fmaxf(1.0f, 2.0f * t * kConeTan);
+  if (t > 16.0f) return 1.0f;
+  const float dia = fmaxf(1.0f, 2.0f * t * kConeTan);
   const int maxl = A.n_levels - 1;
-  float sumA = 0.0f;
-  for (int cone = 0; cone < 6; ++cone) {
-    const float sg = (cone & 1) ? -1.0f : 1.0f;
-    const int ax = cone >> 1;
-    float occl = 0.0f, t = 1.0f;
-    while (t <= 16.0f) {
-      const float dia = fmaxf(1.0f, 2.0f * t * tan_half);
-      float lam = fminf(log2f(dia), (float)maxl);
-      const int l0 = (int)floorf(lam);
-      const float fl = lam - (float)l0;
-      float3 q = P;
-      if (ax == 0) q.x += sg * t; else if (ax == 1) q.y += sg * t; else q.z += sg * t;
-      float s = trilinear(A.mips + A.lev_off[l0], A.g.n >> l0, 1.0f / (float)(1 << l0), q);
-      if (fl > 0.0f && l0 + 1 <= maxl)
-        s = (1.0f - fl) * s +
-            fl * trilinear(A.mips + A.lev_off[l0 + 1], A.g.n >> (l0 + 1), 1.0f / (float)(2 << l0), q);
-      occl = occl + (1.0f - occl) * s;
-      t += dia * 0.5f;
-    }
-    sumA += occl;
-  }
-  return 1.0f - sumA * (1.0f / 6.0f);
+  const float lam = fminf(log2f(dia), (float)maxl);
+  const int l0 = (int)floorf(lam);
+  const float fl = lam - (float)l0;
+  const float sg = (c & 1) ? -1.0f : 1.0f;
+  float3 q = P;
+  const int ax = c >> 1;
+  if (ax == 0) q.x += sg * t; else if (ax == 1) q.y += sg * t; else q.z += sg * t;
+  float s = trilinear(A.mips + A.lev_off[l0], A.g.n >> l0, 1.0f / (float)(1 << l0), q);
+  if (fl > 0.0f && l0 + 1 <= maxl)
+    s = (1.0f - fl) * s +
+        fl * trilinear(A.mips + A.lev_off[l0 + 1], A.g.n >> (l0 + 1), 1.0f / (float)(2 << l0), q);
+  return 1.0f - s;
 }
 
-// ------------------------------------------------------------------ helpers
+// AO at P by one lane: mean over cones of prod_k (1 - s_k).
+__device__ __noinline__ float ao_lane(const TraceArgs& A, float3 P) {
+  float sum = 0.0f;
+  for (int c = 0; c < 6; ++c) {
+    float p = 1.0f;
+    for (int k = 0; k < kConeSteps; ++k) p *= cone_sample_clear(A, P, c, k);
+    sum += p;
+  }
+  return sum * (1.0f / 6.0f);
+}
+
+// AO at P (same P in every lane) by the whole warp: lane 4c + k takes sample k
+// of cone c.
+__device__ __noinline__ float ao_warp(const TraceArgs& A, float3 P) {
+  const int lane = threadIdx.x & 31;
+  float v = lane < 6 * kConeSteps ? cone_sample_clear(A, P, lane / kConeSteps, lane % kConeSteps) : 1.0f;
+  v *= __shfl_xor_sync(FULL, v, 1);
+  v *= __shfl_xor_sync(FULL, v, 2);   // product over the cone's 4 samples
+  float s = (lane < 6 * kConeSteps && (lane & 3) == 0) ? v : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  return s * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ float3 tangent_colour(const TraceArgs& A, uint32_t id) {
+  const float3 a = f3(__ldg(&A.pos[id])), b = f3(__ldg(&A.pos[id + 1]));
+  const float3 dv = b - a;
+  const float l2 = dot3(dv, dv);
+  if (!(l2 > 0.0f)) return make_float3(1.0f, 1.0f, 1.0f);
+  const float il = 1.0f / sqrtf(l2);
+  return make_float3(fabsf(dv.x) * il, fabsf(dv.y) * il, fabsf(dv.z) * il);
+}
+
 __device__ __forceinline__ bool clip_keeps(const TraceArgs& A, float3 P, float4 p0, float4 p1,
                                            uint32_t id) {
   if (__float_as_uint(p0.w) & kClipOn) {
@@ -99,110 +154,124 @@ __device__ __forceinline__ bool clip_keeps(const TraceArgs& A, float3 P, float4 
   return true;
 }
 
-struct RayState {
+// Key of list entry s for ray (o, d) over [t0, t1): depth bits << 32 | id, or
+// ~0 when the segment gives no accepted hit there.
+__device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint32_t s, float3 o,
+                                                        float3 d, float t0, float t1, float r2,
+                                                        float rrm) {
+  const uint32_t id = __ldg(&A.g.lists[s]);
+  if (id + 1 >= A.n_vert) {
+    set_err(A.g.st, kErrBounds);
+    return ~0ull;
+  }
+  const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
+  if (!lines_may_meet(o, d, f3(p0), f3(p1), rrm)) return ~0ull;
+  const float t = capsule_entry(o, d, f3(p0), f3(p1), r2);
+  if (!(t >= t0 && t < t1)) return ~0ull;
+  if (!clip_keeps(A, o + t * d, p0, p1, id)) return ~0ull;
+  return ((unsigned long long)__float_as_uint(t) << 32) | id;
+}
+
+// Per-lane ray state.
+struct Ray {
   float3 o, d;
-  float C[3];
-  float T;
+  float og[3], inv[3];
+  int step[3], v[3];
+  float tcur, t1;
+  float C[3], T;
   int first_id;
   float first_t;
+  uint32_t pix, n_queued;
+  bool active, pending, missed;
+  uint32_t beg, end;   // pending voxel's list
+  float vt0, vt1;      // pending voxel's ray interval
 };
 
-__device__ __forceinline__ void shade(const TraceArgs& A, RayState& R, uint32_t id, float t) {
-  const float3 a = f3(__ldg(&A.pos[id])), b = f3(__ldg(&A.pos[id + 1]));
-  const float3 dv = b - a;
-  const float l2 = dot3(dv, dv);
-  float3 c = make_float3(1.0f, 1.0f, 1.0f);
-  if (l2 > 0.0f) {
-    const float il = 1.0f / sqrtf(l2);
-    c = make_float3(fabsf(dv.x) * il, fabsf(dv.y) * il, fabsf(dv.z) * il);
+// Step the lane's ray to its next voxel that has a list; returns false when the
+// ray leaves the grid (or queues too many culled voxels).
+__device__ bool advance(const TraceArgs& A, Ray& R) {
+  const int n = A.g.n;
+  const int max_steps = 3 * n + 16;
+  for (int it = 0; it < max_steps; ++it) {
+    if (R.tcur > R.t1) return false;
+    const uint32_t bidx = ((uint32_t)(R.v[2] >> 2) << (2 * A.g.log2nb)) |
+                          ((uint32_t)(R.v[1] >> 2) << A.g.log2nb) | (uint32_t)(R.v[0] >> 2);
+    if (!bit_at(A.g.occb, bidx)) {
+      // cross the whole empty brick
+      float tb = __int_as_float(0x7f800000);
+      int kb = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (R.step[k] == 0) continue;
+        const int b0 = R.v[k] & ~3;
+        const float tk = ((float)(R.step[k] > 0 ? b0 + 4 : b0) - R.og[k]) * R.inv[k];
+        if (tk < tb) { tb = tk; kb = k; }
+      }
+      if (tb > R.t1) return false;
+      int nv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int b0 = R.v[k] & ~3;
+        const float dk = cmp3(R.d, k);
+        if (k == kb) nv[k] = R.step[k] > 0 ? b0 + 4 : b0 - 1;
+        else nv[k] = min(b0 + 3, max(b0, (int)floorf(fmaf(tb, dk, R.og[k]))));
+      }
+      if (nv[kb] < 0 || nv[kb] >= n) return false;
+      R.v[0] = nv[0]; R.v[1] = nv[1]; R.v[2] = nv[2];
+      R.tcur = fmaxf(R.tcur, tb);
+      continue;
+    }
+    float texit = __int_as_float(0x7f800000);
+    int ke = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (R.step[k] == 0) continue;
+      const float tk = ((float)(R.step[k] > 0 ? R.v[k] + 1 : R.v[k]) - R.og[k]) * R.inv[k];
+      if (tk < texit) { texit = tk; ke = k; }
+    }
+    const uint32_t idx = brick_index(R.v[0], R.v[1], R.v[2], A.g.log2nb);
+    const uint32_t cnt = __ldg(&A.g.word[idx]) & 0xffffu;
+    const float tin = R.tcur;
+    // step past this voxel before returning, so the next call resumes after it
+    R.tcur = texit;
+    R.v[ke] += R.step[ke];
+    const bool inside = R.v[ke] >= 0 && R.v[ke] < n;
+    if (cnt) {
+      if (!bit_at(A.g.vis, idx)) {
+        // culled voxel on the ray: queue it, march on as if it were empty
+        const uint32_t bm = 1u << (idx & 31);
+        const uint32_t old = atomicOr(&A.need[idx >> 5], bm);
+        if (!(old & bm)) {
+          const uint32_t q = atomicAdd(A.vq_cnt, 1u);
+          if (q < A.vq_cap) A.vq[q] = idx;
+          else set_err(A.g.st, kErrOverflow);
+        }
+        R.missed = true;
+        if (++R.n_queued >= A.max_queue) return false;
+      } else {
+        // a list past the capacity (reported as overflow) is read only up to it
+        const uint32_t end0 = __ldg(&A.g.cur[idx]);
+        if (end0 < cnt) {
+          set_err(A.g.st, kErrBounds);
+          return false;
+        }
+        const uint32_t end = (unsigned long long)end0 > A.g.list_cap ? (uint32_t)A.g.list_cap : end0;
+        R.beg = end0 - cnt < end ? end0 - cnt : end;
+        R.end = end;
+        R.vt0 = tin;
+        R.vt1 = texit;
+        if (!inside) R.t1 = -1.0f;  // this was the last voxel; stop after it
+        return true;
+      }
+    }
+    if (!inside) return false;
   }
-  if (A.ao) {
-    const float ao = ambient_occlusion(A, R.o + t * R.d);
-    c = ao * c;
-  }
-  const float w = R.T * A.alpha;
-  R.C[0] = fmaf(w, c.x, R.C[0]);
-  R.C[1] = fmaf(w, c.y, R.C[1]);
-  R.C[2] = fmaf(w, c.z, R.C[2]);
-  R.T *= (1.0f - A.alpha);
-  if (R.first_id < 0) {
-    R.first_id = (int)id;
-    R.first_t = t;
-  }
+  return false;
 }
 
-// Process one voxel's list over [t0, t1). Returns true when the ray is done.
-template <int K>
-__device__ __forceinline__ bool process_voxel(const TraceArgs& A, RayState& R, uint32_t beg,
-                                              uint32_t end, float t0, float t1) {
-  const float r2 = A.g.r * A.g.r;
-  if (K == 1) {
-    float bt = __int_as_float(0x7f800000);
-    uint32_t bid = 0xffffffffu;
-    for (uint32_t s = beg; s < end; ++s) {
-      const uint32_t id = __ldg(&A.g.lists[s]);
-      if (id + 1 >= A.n_vert) { set_err(A.g.st, kErrBounds); continue; }
-      const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
-      const float t = capsule_entry(R.o, R.d, f3(p0), f3(p1), r2);
-      if (t >= t0 && t < t1 && (t < bt || (t == bt && id < bid)) &&
-          clip_keeps(A, R.o + t * R.d, p0, p1, id)) {
-        bt = t;
-        bid = id;
-      }
-    }
-    if (bid != 0xffffffffu) {
-      shade(A, R, bid, bt);
-      return true;
-    }
-    return false;
-  } else {
-    unsigned long long last = 0ull;
-    bool more = true;
-    while (more) {
-      unsigned long long key[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) key[q] = ~0ull;
-      uint32_t nacc = 0;
-      for (uint32_t s = beg; s < end; ++s) {
-        const uint32_t id = __ldg(&A.g.lists[s]);
-        if (id + 1 >= A.n_vert) { set_err(A.g.st, kErrBounds); continue; }
-        const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
-        const float t = capsule_entry(R.o, R.d, f3(p0), f3(p1), r2);
-        if (!(t >= t0 && t < t1)) continue;
-        const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | id;
-        if (k <= last) continue;
-        if (!clip_keeps(A, R.o + t * R.d, p0, p1, id)) continue;
-        ++nacc;
-        if (k < key[K - 1]) {
-          key[K - 1] = k;
-#pragma unroll
-          for (int q = K - 1; q > 0; --q) {
-            const unsigned long long lo = min(key[q - 1], key[q]), hi = max(key[q - 1], key[q]);
-            key[q - 1] = lo;
-            key[q] = hi;
-          }
-        }
-      }
-      const uint32_t m = min(nacc, (uint32_t)K);
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        if ((uint32_t)q < m && R.T >= kTStop) {
-          shade(A, R, (uint32_t)(key[q] & 0xffffffffu), __uint_as_float((uint32_t)(key[q] >> 32)));
-          last = key[q];
-        }
-      }
-      if (R.T < kTStop) return true;
-      more = nacc > (uint32_t)K;
-    }
-    return false;
-  }
-}
-
-template <int K>
-__device__ void trace_pixel(const TraceArgs& A, int px, int py, uint32_t pix) {
+__device__ void init_ray(const TraceArgs& A, Ray& R, int px, int py, bool valid) {
   const CamDev& c = A.cam;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  RayState R;
   if (c.ortho) {
     R.o = c.o0 + fx * c.ox + fy * c.oy;
     R.d = c.d0;
@@ -215,135 +284,219 @@ __device__ void trace_pixel(const TraceArgs& A, int px, int py, uint32_t pix) {
   R.T = 1.0f;
   R.first_id = -1;
   R.first_t = __int_as_float(0x7f800000);
-
+  R.n_queued = 0;
+  R.missed = false;
+  R.pending = false;
   const int n = A.g.n;
   const float N = (float)n;
-  float inv[3], og[3], dg[3];
-  int step[3];
   float t0 = 0.0f, t1 = __int_as_float(0x7f800000);
-  bool miss = false;
+  bool miss = !valid;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    og[k] = cmp3(R.o, k);
-    dg[k] = cmp3(R.d, k);
-    step[k] = dg[k] > 0.0f ? 1 : (dg[k] < 0.0f ? -1 : 0);
-    if (dg[k] != 0.0f) {
-      inv[k] = 1.0f / dg[k];
-      float ta = (0.0f - og[k]) * inv[k], tb = (N - og[k]) * inv[k];
+    R.og[k] = cmp3(R.o, k);
+    const float dk = cmp3(R.d, k);
+    R.step[k] = dk > 0.0f ? 1 : (dk < 0.0f ? -1 : 0);
+    if (dk != 0.0f) {
+      R.inv[k] = 1.0f / dk;
+      float ta = (0.0f - R.og[k]) * R.inv[k], tb = (N - R.og[k]) * R.inv[k];
       if (ta > tb) { const float q = ta; ta = tb; tb = q; }
       t0 = fmaxf(t0, ta);
       t1 = fminf(t1, tb);
     } else {
-      inv[k] = 0.0f;
-      if (og[k] < 0.0f || og[k] > N) miss = true;
+      R.inv[k] = 0.0f;
+      if (R.og[k] < 0.0f || R.og[k] > N) miss = true;
     }
   }
-  bool missed = false;
-  uint32_t n_queued = 0;
-  if (!miss && t0 <= t1) {
-    int v[3];
+  R.active = !miss && t0 <= t1;
+  R.tcur = t0;
+  R.t1 = t1;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = min(n - 1, max(0, (int)floorf(fmaf(t0, dg[k], og[k]))));
-    float tcur = t0;
-    const int max_steps = 3 * n + 16;
-    for (int it = 0; it < max_steps; ++it) {
-      const uint32_t bidx = ((uint32_t)(v[2] >> 2) << (2 * A.g.log2nb)) |
-                            ((uint32_t)(v[1] >> 2) << A.g.log2nb) | (uint32_t)(v[0] >> 2);
-      if (!bit_at(A.g.occb, bidx)) {
-        // cross the whole empty brick
-        float tb = __int_as_float(0x7f800000);
-        int kb = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if (step[k] == 0) continue;
-          const int b0 = v[k] & ~3;
-          const float tk = ((float)(step[k] > 0 ? b0 + 4 : b0) - og[k]) * inv[k];
-          if (tk < tb) { tb = tk; kb = k; }
-        }
-        if (tb > t1) break;
-        int nv[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int b0 = v[k] & ~3;
-          if (k == kb) nv[k] = step[k] > 0 ? b0 + 4 : b0 - 1;
-          else nv[k] = min(b0 + 3, max(b0, (int)floorf(fmaf(tb, dg[k], og[k]))));
-        }
-        if (nv[kb] < 0 || nv[kb] >= n) break;
-        v[0] = nv[0]; v[1] = nv[1]; v[2] = nv[2];
-        tcur = fmaxf(tcur, tb);
-        continue;
+  for (int k = 0; k < 3; ++k) R.v[k] = min(n - 1, max(0, (int)floorf(fmaf(t0, cmp3(R.d, k), R.og[k]))));
+}
+
+// The warp processes the pending voxel of lane `L`.
+template <bool OPAQUE>
+__device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
+  const int lane = threadIdx.x & 31;
+  const float3 o = shfl3(R.o, L), d = shfl3(R.d, L);
+  const uint32_t beg = __shfl_sync(FULL, R.beg, L), end = __shfl_sync(FULL, R.end, L);
+  const float t0 = __shfl_sync(FULL, R.vt0, L), t1 = __shfl_sync(FULL, R.vt1, L);
+  const float r2 = A.g.r * A.g.r;
+  const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
+  if (OPAQUE) {
+    unsigned long long best = ~0ull;
+    for (uint32_t s = beg + lane; s < end; s += 32) {
+      const unsigned long long k = entry_key(A, s, o, d, t0, t1, r2, rrm);
+      best = k < best ? k : best;
+    }
+    best = warp_min_u64(best);
+    if (best != ~0ull) {
+      const uint32_t id = (uint32_t)(best & 0xffffffffu);
+      const float t = __uint_as_float((uint32_t)(best >> 32));
+      float3 c = tangent_colour(A, id);
+      if (A.ao) c = ao_warp(A, o + t * d) * c;
+      if (lane == L) {
+        R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
+        R.T *= (1.0f - A.alpha);
+        R.first_id = (int)id;
+        R.first_t = t;
+        R.active = false;
       }
-      float texit = __int_as_float(0x7f800000);
-      int ke = 0;
+    }
+    return;
+  }
+  // transparent
+  float T = __shfl_sync(FULL, R.T, L);
+  float C0 = __shfl_sync(FULL, R.C[0], L), C1 = __shfl_sync(FULL, R.C[1], L),
+        C2 = __shfl_sync(FULL, R.C[2], L);
+  int fid = __shfl_sync(FULL, R.first_id, L);
+  float ft = __shfl_sync(FULL, R.first_t, L);
+  const float om = 1.0f - A.alpha;
+  unsigned long long last = 0ull;  // keys <= last are composited
+  bool rescan = true;
+  while (rescan && T >= kTStop) {
+    unsigned long long buf[kLaneKeys];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (step[k] == 0) continue;
-        const float tk = ((float)(step[k] > 0 ? v[k] + 1 : v[k]) - og[k]) * inv[k];
-        if (tk < texit) { texit = tk; ke = k; }
-      }
-      const uint32_t idx = brick_index(v[0], v[1], v[2], A.g.log2nb);
-      const uint32_t cnt = __ldg(&A.g.word[idx]) & 0xffffu;
-      if (cnt) {
-        if (!bit_at(A.g.vis, idx)) {
-          // Culled voxel on the ray: queue it and keep going as if it were
-          // empty. Its hits could only end the ray sooner, so every culled
-          // voxel the ray truly needs lies before the point where this
-          // optimistic march ends and gets queued now; one repair round lists
-          // them all and the pixel is traced again.
-          const uint32_t bm = 1u << (idx & 31);
-          const uint32_t old = atomicOr(&A.need[idx >> 5], bm);
-          if (!(old & bm)) {
-            const uint32_t q = atomicAdd(A.vq_cnt, 1u);
-            if (q < A.vq_cap) A.vq[q] = idx;
-            else set_err(A.g.st, kErrOverflow);
-          }
-          missed = true;
-          if (++n_queued >= A.max_queue) break;
-          tcur = texit;
-          if (tcur > t1) break;
-          v[ke] += step[ke];
-          if (v[ke] < 0 || v[ke] >= n) break;
-          continue;
+    for (int q = 0; q < kLaneKeys; ++q) buf[q] = ~0ull;
+    bool dropped = false;
+    for (uint32_t s = beg + lane; s < end; s += 32) {
+      const unsigned long long k = entry_key(A, s, o, d, t0, t1, r2, rrm);
+      if (k == ~0ull || k <= last) continue;
+      if (k < buf[kLaneKeys - 1]) {
+        if (buf[kLaneKeys - 1] != ~0ull) dropped = true;
+        buf[kLaneKeys - 1] = k;
+#pragma unroll
+        for (int q = kLaneKeys - 1; q > 0; --q) {
+          const unsigned long long lo = buf[q - 1] < buf[q] ? buf[q - 1] : buf[q];
+          const unsigned long long hi = buf[q - 1] < buf[q] ? buf[q] : buf[q - 1];
+          buf[q - 1] = lo;
+          buf[q] = hi;
         }
-        // a list past the capacity (reported as overflow) is read only up to it
-        const uint32_t end0 = __ldg(&A.g.cur[idx]);
-        const uint32_t end = (unsigned long long)end0 > A.g.list_cap ? (uint32_t)A.g.list_cap : end0;
-        const uint32_t beg = end0 - cnt < end ? end0 - cnt : end;
-        if (end0 < cnt) { set_err(A.g.st, kErrBounds); break; }
-        if (process_voxel<K>(A, R, beg, end, tcur, texit)) break;
+      } else {
+        dropped = true;
       }
-      tcur = texit;
-      if (tcur > t1) break;
-      v[ke] += step[ke];
-      if (v[ke] < 0 || v[ke] >= n) break;
+    }
+    // keys up to `lim` are complete: a lane that dropped keys kept its smallest
+    const unsigned long long lim = warp_min_u64(dropped ? buf[kLaneKeys - 1] : ~0ull);
+    rescan = lim != ~0ull;
+    bool more = true;
+    while (more && T >= kTStop) {
+      // extract up to 32 keys in order; lane q receives the q-th
+      unsigned long long mine = ~0ull;
+      int n_out = 0;
+      for (; n_out < 32; ++n_out) {
+        const unsigned long long m = warp_min_u64(buf[0]);
+        if (m == ~0ull || m > lim) break;
+        if (buf[0] == m) {
+#pragma unroll
+          for (int q = 0; q < kLaneKeys - 1; ++q) buf[q] = buf[q + 1];
+          buf[kLaneKeys - 1] = ~0ull;
+        }
+        if (lane == n_out) mine = m;
+      }
+      more = n_out == 32;
+      if (n_out == 0) break;
+      // shade in parallel
+      float3 c = make_float3(0.f, 0.f, 0.f);
+      float tq = 0.0f;
+      if (lane < n_out) {
+        const uint32_t id = (uint32_t)(mine & 0xffffffffu);
+        tq = __uint_as_float((uint32_t)(mine >> 32));
+        c = tangent_colour(A, id);
+        if (A.ao) c = ao_lane(A, o + tq * d) * c;
+      }
+      // accumulate in key order
+      for (int q = 0; q < n_out; ++q) {
+        const float3 cq = shfl3(c, q);
+        const unsigned long long kq = __shfl_sync(FULL, mine, q);
+        if (T < kTStop) break;
+        const float w = T * A.alpha;
+        C0 = fmaf(w, cq.x, C0);
+        C1 = fmaf(w, cq.y, C1);
+        C2 = fmaf(w, cq.z, C2);
+        T *= om;
+        if (fid < 0) {
+          fid = (int)(kq & 0xffffffffu);
+          ft = __uint_as_float((uint32_t)(kq >> 32));
+        }
+        last = kq;
+      }
+    }
+    // a rescan is needed only when the extraction stopped at the drop limit
+    rescan = rescan && T >= kTStop && last == lim;
+  }
+  if (lane == L) {
+    R.T = T;
+    R.C[0] = C0; R.C[1] = C1; R.C[2] = C2;
+    R.first_id = fid;
+    R.first_t = ft;
+    if (T < kTStop) R.active = false;
+  }
+}
+
+template <bool OPAQUE>
+__device__ void trace_warp(const TraceArgs& A, Ray& R) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    if (R.active && !R.pending) {
+      R.pending = advance(A, R);
+      if (!R.pending) R.active = false;
+    }
+    unsigned pm = __ballot_sync(FULL, R.pending);
+    if (!pm) break;
+    while (pm) {
+      const int L = __ffs(pm) - 1;
+      pm &= pm - 1;
+      process_voxel<OPAQUE>(A, R, L);
+      if (lane == L) {
+        R.pending = false;
+        if (R.t1 < 0.0f) R.active = false;
+      }
     }
   }
-  if (missed) {
+}
+
+__device__ __forceinline__ void finish(const TraceArgs& A, const Ray& R, bool valid) {
+  if (!valid) return;
+  if (R.missed) {
     const uint32_t q = atomicAdd(A.pq_cnt, 1u);
-    if (q < A.pq_cap) A.pq[q] = pix;
+    if (q < A.pq_cap) A.pq[q] = R.pix;
     else set_err(A.g.st, kErrOverflow);
     return;
   }
-  A.rgba[pix] = make_float4(R.C[0], R.C[1], R.C[2], 1.0f - R.T);
-  if (A.first_id) A.first_id[pix] = R.first_id;
-  if (A.first_t) A.first_t[pix] = R.first_t;
+  A.rgba[R.pix] = make_float4(R.C[0], R.C[1], R.C[2], 1.0f - R.T);
+  if (A.first_id) A.first_id[R.pix] = R.first_id;
+  if (A.first_t) A.first_t[R.pix] = R.first_t;
 }
 
-template <int K>
+template <bool OPAQUE>
 __global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
+  const int lane = threadIdx.x & 31;
+  Ray R;
   if (A.pix_list) {
+    // repair re-trace: warps take 32 queued pixels at a time
     const uint32_t cnt = min(*A.pix_count, A.pq_cap);
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
-      const uint32_t pix = A.pix_list[q];
-      trace_pixel<K>(A, (int)(pix % (uint32_t)A.cam.width), (int)(pix / (uint32_t)A.cam.width), pix);
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < cnt;
+         base += warps * 32) {
+      const uint32_t q = base + lane;
+      const bool valid = q < cnt;
+      const uint32_t pix = valid ? A.pix_list[q] : 0u;
+      R.pix = pix;
+      init_ray(A, R, (int)(pix % (uint32_t)A.cam.width), (int)(pix / (uint32_t)A.cam.width), valid);
+      trace_warp<OPAQUE>(A, R);
+      finish(A, R, valid);
     }
     return;
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
   const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-  if (px >= A.cam.width || py >= A.cam.height) return;
-  trace_pixel<K>(A, px, py, (uint32_t)(py * A.cam.width + px));
+  const bool valid = px < A.cam.width && py < A.cam.height;
+  R.pix = valid ? (uint32_t)(py * A.cam.width + px) : 0u;
+  init_ray(A, R, px, py, valid);
+  trace_warp<OPAQUE>(A, R);
+  finish(A, R, valid);
 }
 
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
@@ -353,22 +506,19 @@ int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
   } else {
     grid = dim3((a.cam.width + 15) / 16, (a.cam.height + 7) / 8);
   }
-  switch (K) {
-    case 1: k_trace<1><<<grid, block, 0, s>>>(a); break;
-    case 8: k_trace<8><<<grid, block, 0, s>>>(a); break;
-    case 16: k_trace<16><<<grid, block, 0, s>>>(a); break;
-    default: k_trace<32><<<grid, block, 0, s>>>(a); break;
-  }
+  if (K == 1) k_trace<true><<<grid, block, 0, s>>>(a);
+  else k_trace<false><<<grid, block, 0, s>>>(a);
   return 1;
 }
 
 // ----------------------------------------------------------------- repair
 __global__ void k_repair_alloc(GridDev g, uint32_t* needb, const uint32_t* vq, const uint32_t* vq_cnt,
-                               uint32_t vq_cap) {
+                               const uint32_t* pq_cnt, uint32_t vq_cap) {
   const uint32_t nq = min(*vq_cnt, vq_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0 && nq) {
     atomicAdd(&g.st->repair_rounds, 1u);
     atomicAdd(&g.st->repaired_voxels, nq);
+    atomicAdd(&g.st->retraced_pixels, *pq_cnt);
   }
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
     const uint32_t idx = vq[q];
@@ -397,8 +547,9 @@ __global__ void k_repair_clear(GridDev g, uint32_t* need, const uint32_t* vq, co
 }
 
 int launch_repair_alloc(const GridDev& g, uint32_t* needb, const uint32_t* vq,
-                         const uint32_t* vq_cnt, uint32_t vq_cap, cudaStream_t s) {
-  k_repair_alloc<<<152, 256, 0, s>>>(g, needb, vq, vq_cnt, vq_cap);
+                        const uint32_t* vq_cnt, const uint32_t* pq_cnt, uint32_t vq_cap,
+                        cudaStream_t s) {
+  k_repair_alloc<<<152, 256, 0, s>>>(g, needb, vq, vq_cnt, pq_cnt, vq_cap);
   return 1;
 }
 

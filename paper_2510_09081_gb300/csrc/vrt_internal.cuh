@@ -41,6 +41,8 @@ struct DevStatus {
   unsigned long long sum_count_field;  // checked by the scan
   unsigned long long sum_occ_field;
   unsigned long long listed;         // entries written by pass 2 and repairs
+  unsigned int xq_cnt;               // undecided (segment, voxel) pairs of the current pass
+  unsigned int xq_pad;
   unsigned int list_tail;            // next free list entry (scan total + repairs)
   unsigned int visible_voxels;
   unsigned int max_count;
@@ -49,6 +51,8 @@ struct DevStatus {
   unsigned int pq_cnt[2];            // pixels to trace again (ping-pong per round)
   unsigned int repaired_voxels;
   unsigned int repair_rounds;
+  unsigned int retraced_pixels;
+  unsigned int pad_;
 };
 
 // -------------------------------------------------------------- grid layout
@@ -76,6 +80,8 @@ struct GridDev {
   uint32_t* occb;          // [bricks / 32] brick has an occupied voxel
   uint32_t* lists;         // [list_cap]
   unsigned long long list_cap;
+  uint2* xq;               // [xq_cap] undecided (segment id, packed voxel) pairs
+  uint32_t xq_cap;
   DevStatus* st;
 };
 
@@ -240,21 +246,30 @@ static __device__ __noinline__ bool seg_box_exact(const long long* A, const long
   return false;
 }
 
-// Full decision for voxel (x, y, z): filter, then the exact path if needed.
-// a, b are the snapped global endpoints.
-__device__ __forceinline__ bool seg_in_voxel(float3 a, float3 b, int x, int y, int z, float rl,
-                                             int RL, int force_exact, unsigned long long* n_exact) {
+// Filter decision for voxel (x, y, z): 1 within, 0 not, -1 undecided. a, b
+// are the snapped global endpoints (local coordinates are exact in fp32).
+__device__ __forceinline__ int seg_filter_at(float3 a, float3 b, int x, int y, int z, float rl) {
   const float3 la = make_float3(a.x - (float)x, a.y - (float)y, a.z - (float)z);
-  const float3 ld = b - a;
-  int dec = force_exact ? -1 : seg_box_filter(la, ld, rl);
-  if (dec >= 0) return dec == 1;
-  ++*n_exact;
+  return seg_box_filter(la, b - a, rl);
+}
+
+// Exact decision for voxel (x, y, z) on the 2^-14 lattice.
+__device__ __forceinline__ bool seg_exact_at(float3 a, float3 b, int x, int y, int z, int RL) {
+  const float3 la = make_float3(a.x - (float)x, a.y - (float)y, a.z - (float)z);
   const long long A[3] = {__float2ll_rn(la.x * kUnits), __float2ll_rn(la.y * kUnits),
                           __float2ll_rn(la.z * kUnits)};
   const long long D[3] = {__float2ll_rn(b.x * kUnits) - __float2ll_rn(a.x * kUnits),
                           __float2ll_rn(b.y * kUnits) - __float2ll_rn(a.y * kUnits),
                           __float2ll_rn(b.z * kUnits) - __float2ll_rn(a.z * kUnits)};
   return seg_box_exact(A, D, (long long)kUnits, (long long)RL);
+}
+
+// (segment, voxel) pairs the filter could not decide, packed for the exact pass.
+__device__ __forceinline__ uint32_t pack_voxel(int x, int y, int z) {
+  return (uint32_t)x | ((uint32_t)y << 10) | ((uint32_t)z << 20);
+}
+__device__ __forceinline__ void unpack_voxel(uint32_t p, int& x, int& y, int& z) {
+  x = (int)(p & 1023u); y = (int)((p >> 10) & 1023u); z = (int)(p >> 20);
 }
 
 // ------------------------------------------------------------- Alg. 2 and 3
@@ -274,6 +289,19 @@ __device__ __forceinline__ float capsule_occupancy(float3 p, float3 a, float3 b,
 }
 
 // ------------------------------------------------------------ ray / capsule
+// Can the line o + t d come within r of the segment [a, b]? A hit needs the
+// two lines within r of each other: with n = d x (b - a), their distance is
+// |(o - a) . n| / |n|. Conservative (margin 1e-3 voxel on r; nearly parallel
+// lines always pass), so it only skips capsules the full test would miss.
+__device__ __forceinline__ bool lines_may_meet(float3 o, float3 d, float3 a, float3 b, float rr_margin) {
+  const float3 ba = b - a;
+  const float3 n = make_float3(d.y * ba.z - d.z * ba.y, d.z * ba.x - d.x * ba.z, d.x * ba.y - d.y * ba.x);
+  const float nn = dot3(n, n);
+  if (!(nn > 1e-4f * dot3(ba, ba))) return true;
+  const float s = dot3(o - a, n);
+  return s * s <= rr_margin * nn;
+}
+
 // First entry of the line o + t d (|d| = 1) into the capsule (a, b, r): the
 // smallest entry over the two end balls and the curved side of the finite
 // cylinder (its flat ends lie inside the balls). +inf when the line misses.
