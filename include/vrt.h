@@ -108,6 +108,11 @@ typedef struct {
   uint64_t kernel_launches;  /* kernels launched by this grid since creation */
   uint32_t retraced_pixels;  /* pixels traced again by the last frame's repair */
   uint32_t reserved;
+  /* trace work, counted only while VRT_OPT_TRACE_COUNTERS is on (cumulative): */
+  uint64_t trace_entries;       /* list entries examined */
+  uint64_t trace_capsule_tests; /* entries that passed the line-distance test */
+  uint64_t trace_voxels;        /* voxel lists processed */
+  uint64_t trace_steps;         /* DDA steps (voxels and empty bricks) */
 } vrt_stats;
 
 /* Create a grid (Sec. 3.1). `cuda_stream` is a cudaStream_t (NULL = legacy
@@ -188,9 +193,12 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
 /* Options. VRT_OPT_FORCE_EXACT (1): value 1 decides every list membership on
  * the exact integer path instead of the fp32 filter (for testing).
  * VRT_OPT_STAGE_TIMING (2): value 1 records CUDA events on the grid's stream
- * around each stage (see vrt_get_stage_ms). */
+ * around each stage (see vrt_get_stage_ms).
+ * VRT_OPT_TRACE_COUNTERS (3): value 1 runs an instrumented trace that counts
+ * its work into vrt_stats (slower; for analysis). */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
+#define VRT_OPT_TRACE_COUNTERS 3
 vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value);
 
 /* Stage durations of the last frame in milliseconds (waits), measured with

@@ -23,6 +23,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_OVERFLOW, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ER
 STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "OVERFLOW", "CUDA", "TIMEOUT", "STATE", "BOUNDS"]
 OPT_FORCE_EXACT = 1
 OPT_STAGE_TIMING = 2
+OPT_TRACE_COUNTERS = 3
 STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
 
 # Exported symbols of the C ABI (include/vrt.h)
@@ -62,7 +63,9 @@ class StatsC(ctypes.Structure):
                 ("repaired_voxels", ctypes.c_uint32), ("repair_rounds", ctypes.c_uint32),
                 ("max_count", ctypes.c_uint32), ("status_bits", ctypes.c_uint32),
                 ("kernel_launches", ctypes.c_uint64), ("retraced_pixels", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("reserved", ctypes.c_uint32), ("trace_entries", ctypes.c_uint64),
+                ("trace_capsule_tests", ctypes.c_uint64), ("trace_voxels", ctypes.c_uint64),
+                ("trace_steps", ctypes.c_uint64)]
 
 
 def load():

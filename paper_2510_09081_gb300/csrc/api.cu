@@ -47,6 +47,7 @@ struct vrt_grid_s {
   uint32_t pq_cap = 0;
   DevStatus* st = nullptr;
   int force_exact = 0;
+  int trace_counters = 0;
   // stage timing
   unsigned long long launches = 0;  // kernels launched by this grid
   bool timing = false;
@@ -477,6 +478,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   make_camdev(host_cam(cam), a.cam);
   a.pos = g->pos; a.nrm = g->nrm;
   a.n_vert = (uint32_t)g->V;
+  a.count = g->trace_counters;
   a.alpha = p->alpha; a.ao = p->ao_cones ? 1 : 0;
   a.mips = g->mips;
   for (int l = 0; l < 11; ++l) a.lev_off[l] = g->lev_off[l];
@@ -495,6 +497,9 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.max_queue = kMaxRepairRounds >= 2 ? kRayQueueLimit : 0xffffffffu;
   VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, vq_cnt), 0,
                               4 * sizeof(unsigned int), g->stream));
+  VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, tr_next), 0,
+                              sizeof(unsigned int) * (kMaxRepairRounds + 1), g->stream));
+  a.work_next = &g->st->tr_next[0];
   stage_mark(g, ST_TRACE, 0);
   g->launches += launch_trace(a, K, g->stream);
   stage_mark(g, ST_TRACE, 1);
@@ -517,6 +522,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
       b.vq = g->vq[nx]; b.vq_cnt = &g->st->vq_cnt[nx];
       b.pq = g->pq[nx]; b.pq_cnt = &g->st->pq_cnt[nx];
       b.max_queue = (r + 2 >= kMaxRepairRounds) ? 0xffffffffu : kRayQueueLimit;
+      b.work_next = &g->st->tr_next[r + 1];
       g->launches += launch_trace(b, K, g->stream);
     }
     stage_mark(g, ST_REPAIR, 1);
@@ -558,6 +564,10 @@ vrt_status vrt_get_stats(vrt_grid g, vrt_stats* out) {
   out->status_bits = hs.err;
   out->kernel_launches = g->launches;
   out->retraced_pixels = hs.retraced_pixels;
+  out->trace_entries = hs.tr_entries;
+  out->trace_capsule_tests = hs.tr_capsule;
+  out->trace_voxels = hs.tr_voxels;
+  out->trace_steps = hs.tr_steps;
   return VRT_OK;
 }
 
@@ -616,6 +626,10 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
   if (option == VRT_OPT_FORCE_EXACT) {
     g->force_exact = value ? 1 : 0;
     return g->V_alloc ? size_exact_queue(g) : VRT_OK;
+  }
+  if (option == VRT_OPT_TRACE_COUNTERS) {
+    g->trace_counters = value ? 1 : 0;
+    return VRT_OK;
   }
   if (option == VRT_OPT_STAGE_TIMING) {
     if (value && !g->ev[0][0])

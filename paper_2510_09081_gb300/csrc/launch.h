@@ -44,6 +44,8 @@ struct TraceArgs {
   uint32_t* pq_cnt;
   uint32_t vq_cap, pq_cap;
   uint32_t max_queue;        // culled voxels one ray may queue before it stops
+  uint32_t* work_next;       // next work item (persistent warps)
+  int count;                 // accumulate trace work counters
 };
 
 int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,

@@ -40,7 +40,10 @@
 namespace vrt {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kLaneKeys = 4;              // transparent: keys kept per lane per scan
+constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
+constexpr int kOwnKeys = 32;              // transparent, own list: keys kept per scan (shared memory)
+constexpr int kTraceThreads = 128;
+constexpr uint32_t kShortList = 64;       // lists up to this length are processed by their own lane
 constexpr float kConeTan = 1.1180340f;    // tan(half angle), cos(half angle) = 2/3
 constexpr int kConeSteps = 4;             // samples per cone: t = 1, 2.118, 4.486, 9.502 (<= 16)
 
@@ -156,9 +159,10 @@ __device__ __forceinline__ bool clip_keeps(const TraceArgs& A, float3 P, float4 
 
 // Key of list entry s for ray (o, d) over [t0, t1): depth bits << 32 | id, or
 // ~0 when the segment gives no accepted hit there.
+template <bool COUNT>
 __device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint32_t s, float3 o,
                                                         float3 d, float t0, float t1, float r2,
-                                                        float rrm) {
+                                                        float rrm, unsigned& n_cap) {
   const uint32_t id = __ldg(&A.g.lists[s]);
   if (id + 1 >= A.n_vert) {
     set_err(A.g.st, kErrBounds);
@@ -166,17 +170,19 @@ __device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint
   }
   const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
   if (!lines_may_meet(o, d, f3(p0), f3(p1), rrm)) return ~0ull;
+  if (COUNT) ++n_cap;
   const float t = capsule_entry(o, d, f3(p0), f3(p1), r2);
   if (!(t >= t0 && t < t1)) return ~0ull;
   if (!clip_keeps(A, o + t * d, p0, p1, id)) return ~0ull;
   return ((unsigned long long)__float_as_uint(t) << 32) | id;
 }
 
-// Per-lane ray state.
+// Per-lane ray state. Components are kept as scalars (no runtime-indexed
+// arrays) so the DDA state stays in registers.
 struct Ray {
-  float3 o, d;
-  float og[3], inv[3];
-  int step[3], v[3];
+  float3 o, d, inv, ooi;  // ooi = o * inv: the boundary b is crossed at b * inv - ooi
+  int sx, sy, sz;      // step direction per axis (-1, 0, 1)
+  int vx, vy, vz;      // current voxel
   float tcur, t1;
   float C[3], T;
   int first_id;
@@ -185,57 +191,70 @@ struct Ray {
   bool active, pending, missed;
   uint32_t beg, end;   // pending voxel's list
   float vt0, vt1;      // pending voxel's ray interval
+  unsigned n_steps, n_entries, n_cap, n_vox;  // work counters
 };
+
+// Parameter where the ray leaves coordinate range [lo, hi] along an axis
+// (the side it moves toward); +inf when it does not move on that axis.
+__device__ __forceinline__ float exit_t(int s, int lo, int hi, float ooi, float inv) {
+  return s != 0 ? fmaf((float)(s > 0 ? hi : lo), inv, -ooi) : __int_as_float(0x7f800000);
+}
 
 // Step the lane's ray to its next voxel that has a list; returns false when the
 // ray leaves the grid (or queues too many culled voxels).
+template <bool COUNT>
 __device__ bool advance(const TraceArgs& A, Ray& R) {
   const int n = A.g.n;
   const int max_steps = 3 * n + 16;
   for (int it = 0; it < max_steps; ++it) {
     if (R.tcur > R.t1) return false;
-    const uint32_t bidx = ((uint32_t)(R.v[2] >> 2) << (2 * A.g.log2nb)) |
-                          ((uint32_t)(R.v[1] >> 2) << A.g.log2nb) | (uint32_t)(R.v[0] >> 2);
+    if (COUNT) ++R.n_steps;
+    const uint32_t bidx = ((uint32_t)(R.vz >> 2) << (2 * A.g.log2nb)) |
+                          ((uint32_t)(R.vy >> 2) << A.g.log2nb) | (uint32_t)(R.vx >> 2);
     if (!bit_at(A.g.occb, bidx)) {
       // cross the whole empty brick
-      float tb = __int_as_float(0x7f800000);
-      int kb = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (R.step[k] == 0) continue;
-        const int b0 = R.v[k] & ~3;
-        const float tk = ((float)(R.step[k] > 0 ? b0 + 4 : b0) - R.og[k]) * R.inv[k];
-        if (tk < tb) { tb = tk; kb = k; }
-      }
+      const int bx = R.vx & ~3, by = R.vy & ~3, bz = R.vz & ~3;
+      const float tx = exit_t(R.sx, bx, bx + 4, R.ooi.x, R.inv.x);
+      const float ty = exit_t(R.sy, by, by + 4, R.ooi.y, R.inv.y);
+      const float tz = exit_t(R.sz, bz, bz + 4, R.ooi.z, R.inv.z);
+      const float tb = fminf(tx, fminf(ty, tz));
       if (tb > R.t1) return false;
-      int nv[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int b0 = R.v[k] & ~3;
-        const float dk = cmp3(R.d, k);
-        if (k == kb) nv[k] = R.step[k] > 0 ? b0 + 4 : b0 - 1;
-        else nv[k] = min(b0 + 3, max(b0, (int)floorf(fmaf(tb, dk, R.og[k]))));
+      const int cx = min(bx + 3, max(bx, (int)floorf(fmaf(tb, R.d.x, R.o.x))));
+      const int cy = min(by + 3, max(by, (int)floorf(fmaf(tb, R.d.y, R.o.y))));
+      const int cz = min(bz + 3, max(bz, (int)floorf(fmaf(tb, R.d.z, R.o.z))));
+      if (tb == tx) {
+        R.vx = R.sx > 0 ? bx + 4 : bx - 1; R.vy = cy; R.vz = cz;
+        if (R.vx < 0 || R.vx >= n) return false;
+      } else if (tb == ty) {
+        R.vy = R.sy > 0 ? by + 4 : by - 1; R.vx = cx; R.vz = cz;
+        if (R.vy < 0 || R.vy >= n) return false;
+      } else {
+        R.vz = R.sz > 0 ? bz + 4 : bz - 1; R.vx = cx; R.vy = cy;
+        if (R.vz < 0 || R.vz >= n) return false;
       }
-      if (nv[kb] < 0 || nv[kb] >= n) return false;
-      R.v[0] = nv[0]; R.v[1] = nv[1]; R.v[2] = nv[2];
       R.tcur = fmaxf(R.tcur, tb);
       continue;
     }
-    float texit = __int_as_float(0x7f800000);
-    int ke = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (R.step[k] == 0) continue;
-      const float tk = ((float)(R.step[k] > 0 ? R.v[k] + 1 : R.v[k]) - R.og[k]) * R.inv[k];
-      if (tk < texit) { texit = tk; ke = k; }
-    }
-    const uint32_t idx = brick_index(R.v[0], R.v[1], R.v[2], A.g.log2nb);
+    const float tx = exit_t(R.sx, R.vx, R.vx + 1, R.ooi.x, R.inv.x);
+    const float ty = exit_t(R.sy, R.vy, R.vy + 1, R.ooi.y, R.inv.y);
+    const float tz = exit_t(R.sz, R.vz, R.vz + 1, R.ooi.z, R.inv.z);
+    const float texit = fminf(tx, fminf(ty, tz));
+    const uint32_t idx = brick_index(R.vx, R.vy, R.vz, A.g.log2nb);
     const uint32_t cnt = __ldg(&A.g.word[idx]) & 0xffffu;
     const float tin = R.tcur;
     // step past this voxel before returning, so the next call resumes after it
     R.tcur = texit;
-    R.v[ke] += R.step[ke];
-    const bool inside = R.v[ke] >= 0 && R.v[ke] < n;
+    bool inside;
+    if (texit == tx) {
+      R.vx += R.sx;
+      inside = R.vx >= 0 && R.vx < n;
+    } else if (texit == ty) {
+      R.vy += R.sy;
+      inside = R.vy >= 0 && R.vy < n;
+    } else {
+      R.vz += R.sz;
+      inside = R.vz >= 0 && R.vz < n;
+    }
     if (cnt) {
       if (!bit_at(A.g.vis, idx)) {
         // culled voxel on the ray: queue it, march on as if it were empty
@@ -285,37 +304,40 @@ __device__ void init_ray(const TraceArgs& A, Ray& R, int px, int py, bool valid)
   R.first_id = -1;
   R.first_t = __int_as_float(0x7f800000);
   R.n_queued = 0;
+  R.n_steps = R.n_entries = R.n_cap = R.n_vox = 0;
   R.missed = false;
   R.pending = false;
-  const int n = A.g.n;
-  const float N = (float)n;
+  const float N = (float)A.g.n;
   float t0 = 0.0f, t1 = __int_as_float(0x7f800000);
   bool miss = !valid;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    R.og[k] = cmp3(R.o, k);
-    const float dk = cmp3(R.d, k);
-    R.step[k] = dk > 0.0f ? 1 : (dk < 0.0f ? -1 : 0);
-    if (dk != 0.0f) {
-      R.inv[k] = 1.0f / dk;
-      float ta = (0.0f - R.og[k]) * R.inv[k], tb = (N - R.og[k]) * R.inv[k];
+  auto axis = [&](float o, float d, int& s, float& inv) {
+    s = d > 0.0f ? 1 : (d < 0.0f ? -1 : 0);
+    if (d != 0.0f) {
+      inv = 1.0f / d;
+      float ta = (0.0f - o) * inv, tb = (N - o) * inv;
       if (ta > tb) { const float q = ta; ta = tb; tb = q; }
       t0 = fmaxf(t0, ta);
       t1 = fminf(t1, tb);
     } else {
-      R.inv[k] = 0.0f;
-      if (R.og[k] < 0.0f || R.og[k] > N) miss = true;
+      inv = 0.0f;
+      if (o < 0.0f || o > N) miss = true;
     }
-  }
+  };
+  axis(R.o.x, R.d.x, R.sx, R.inv.x);
+  axis(R.o.y, R.d.y, R.sy, R.inv.y);
+  axis(R.o.z, R.d.z, R.sz, R.inv.z);
+  R.ooi = make_float3(R.o.x * R.inv.x, R.o.y * R.inv.y, R.o.z * R.inv.z);
   R.active = !miss && t0 <= t1;
   R.tcur = t0;
   R.t1 = t1;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) R.v[k] = min(n - 1, max(0, (int)floorf(fmaf(t0, cmp3(R.d, k), R.og[k]))));
+  const int n = A.g.n;
+  R.vx = min(n - 1, max(0, (int)floorf(fmaf(t0, R.d.x, R.o.x))));
+  R.vy = min(n - 1, max(0, (int)floorf(fmaf(t0, R.d.y, R.o.y))));
+  R.vz = min(n - 1, max(0, (int)floorf(fmaf(t0, R.d.z, R.o.z))));
 }
 
 // The warp processes the pending voxel of lane `L`.
-template <bool OPAQUE>
+template <bool OPAQUE, bool COUNT>
 __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   const int lane = threadIdx.x & 31;
   const float3 o = shfl3(R.o, L), d = shfl3(R.d, L);
@@ -323,12 +345,18 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   const float t0 = __shfl_sync(FULL, R.vt0, L), t1 = __shfl_sync(FULL, R.vt1, L);
   const float r2 = A.g.r * A.g.r;
   const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
+  unsigned n_cap = 0;
+  if (COUNT && lane == L) {
+    ++R.n_vox;
+    R.n_entries += end - beg;
+  }
   if (OPAQUE) {
     unsigned long long best = ~0ull;
     for (uint32_t s = beg + lane; s < end; s += 32) {
-      const unsigned long long k = entry_key(A, s, o, d, t0, t1, r2, rrm);
+      const unsigned long long k = entry_key<COUNT>(A, s, o, d, t0, t1, r2, rrm, n_cap);
       best = k < best ? k : best;
     }
+    if (COUNT) R.n_cap += n_cap;
     best = warp_min_u64(best);
     if (best != ~0ull) {
       const uint32_t id = (uint32_t)(best & 0xffffffffu);
@@ -360,7 +388,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
     for (int q = 0; q < kLaneKeys; ++q) buf[q] = ~0ull;
     bool dropped = false;
     for (uint32_t s = beg + lane; s < end; s += 32) {
-      const unsigned long long k = entry_key(A, s, o, d, t0, t1, r2, rrm);
+      const unsigned long long k = entry_key<COUNT>(A, s, o, d, t0, t1, r2, rrm, n_cap);
       if (k == ~0ull || k <= last) continue;
       if (k < buf[kLaneKeys - 1]) {
         if (buf[kLaneKeys - 1] != ~0ull) dropped = true;
@@ -425,6 +453,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
     // a rescan is needed only when the extraction stopped at the drop limit
     rescan = rescan && T >= kTStop && last == lim;
   }
+  if (COUNT) R.n_cap += n_cap;
   if (lane == L) {
     R.T = T;
     R.C[0] = C0; R.C[1] = C1; R.C[2] = C2;
@@ -434,20 +463,104 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   }
 }
 
-template <bool OPAQUE>
+// A lane processes its own pending voxel (short lists): same acceptance and
+// (depth, id) order as the shared path, with the keys in registers.
+template <bool OPAQUE, bool COUNT>
+__device__ void process_own(const TraceArgs& A, Ray& R) {
+  const float r2 = A.g.r * A.g.r;
+  const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
+  unsigned n_cap = 0;
+  if (COUNT) {
+    ++R.n_vox;
+    R.n_entries += R.end - R.beg;
+  }
+  if (OPAQUE) {
+    unsigned long long best = ~0ull;
+    for (uint32_t s = R.beg; s < R.end; ++s) {
+      const unsigned long long k = entry_key<COUNT>(A, s, R.o, R.d, R.vt0, R.vt1, r2, rrm, n_cap);
+      best = k < best ? k : best;
+    }
+    if (COUNT) R.n_cap += n_cap;
+    if (best != ~0ull) {
+      const uint32_t id = (uint32_t)(best & 0xffffffffu);
+      const float t = __uint_as_float((uint32_t)(best >> 32));
+      float3 c = tangent_colour(A, id);
+      if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
+      R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
+      R.T *= (1.0f - A.alpha);
+      R.first_id = (int)id;
+      R.first_t = t;
+      R.active = false;
+    }
+    return;
+  }
+  // this lane's sorted keys: key q at s_key[q * kTraceThreads + threadIdx.x]
+  extern __shared__ unsigned long long s_key[];
+  unsigned long long* kb = s_key + threadIdx.x;
+  const float om = 1.0f - A.alpha;
+  unsigned long long last = 0ull;
+  for (;;) {
+    uint32_t nacc = 0;
+    int nk = 0;
+    for (uint32_t s = R.beg; s < R.end; ++s) {
+      const unsigned long long k = entry_key<COUNT>(A, s, R.o, R.d, R.vt0, R.vt1, r2, rrm, n_cap);
+      if (k == ~0ull || k <= last) continue;
+      ++nacc;
+      if (nk == kOwnKeys && k >= kb[(kOwnKeys - 1) * kTraceThreads]) continue;
+      int q = nk < kOwnKeys ? nk++ : kOwnKeys - 1;
+      while (q > 0 && kb[(q - 1) * kTraceThreads] > k) {
+        kb[q * kTraceThreads] = kb[(q - 1) * kTraceThreads];
+        --q;
+      }
+      kb[q * kTraceThreads] = k;
+    }
+    for (int q = 0; q < nk && R.T >= kTStop; ++q) {
+      const unsigned long long kq = kb[q * kTraceThreads];
+      const uint32_t id = (uint32_t)(kq & 0xffffffffu);
+      const float t = __uint_as_float((uint32_t)(kq >> 32));
+      float3 c = tangent_colour(A, id);
+      if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
+      const float w = R.T * A.alpha;
+      R.C[0] = fmaf(w, c.x, R.C[0]);
+      R.C[1] = fmaf(w, c.y, R.C[1]);
+      R.C[2] = fmaf(w, c.z, R.C[2]);
+      R.T *= om;
+      if (R.first_id < 0) {
+        R.first_id = (int)id;
+        R.first_t = t;
+      }
+      last = kq;
+    }
+    if (R.T < kTStop) {
+      R.active = false;
+      break;
+    }
+    if (nacc <= (uint32_t)kOwnKeys) break;
+  }
+  if (COUNT) R.n_cap += n_cap;
+}
+
+template <bool OPAQUE, bool COUNT>
 __device__ void trace_warp(const TraceArgs& A, Ray& R) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     if (R.active && !R.pending) {
-      R.pending = advance(A, R);
+      R.pending = advance<COUNT>(A, R);
       if (!R.pending) R.active = false;
     }
+    if (!__any_sync(FULL, R.pending)) break;
+    // short lists: every such lane at once, each on its own list
+    if (R.pending && R.end - R.beg <= kShortList) {
+      process_own<OPAQUE, COUNT>(A, R);
+      R.pending = false;
+      if (R.t1 < 0.0f) R.active = false;
+    }
+    // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
-    if (!pm) break;
     while (pm) {
       const int L = __ffs(pm) - 1;
       pm &= pm - 1;
-      process_voxel<OPAQUE>(A, R, L);
+      process_voxel<OPAQUE, COUNT>(A, R, L);
       if (lane == L) {
         R.pending = false;
         if (R.t1 < 0.0f) R.active = false;
@@ -456,7 +569,24 @@ __device__ void trace_warp(const TraceArgs& A, Ray& R) {
   }
 }
 
+template <bool COUNT>
 __device__ __forceinline__ void finish(const TraceArgs& A, const Ray& R, bool valid) {
+  if (COUNT) {
+    unsigned long long e = R.n_entries, c = R.n_cap, v = R.n_vox, st = R.n_steps;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(FULL, e, o);
+      c += __shfl_xor_sync(FULL, c, o);
+      v += __shfl_xor_sync(FULL, v, o);
+      st += __shfl_xor_sync(FULL, st, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&A.g.st->tr_entries, e);
+      atomicAdd(&A.g.st->tr_capsule, c);
+      atomicAdd(&A.g.st->tr_voxels, v);
+      atomicAdd(&A.g.st->tr_steps, st);
+    }
+  }
   if (!valid) return;
   if (R.missed) {
     const uint32_t q = atomicAdd(A.pq_cnt, 1u);
@@ -469,45 +599,174 @@ __device__ __forceinline__ void finish(const TraceArgs& A, const Ray& R, bool va
   if (A.first_t) A.first_t[R.pix] = R.first_t;
 }
 
-template <bool OPAQUE>
-__global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
+// Transparent main trace: each warp owns one fixed 8x4 tile (a block 2x2
+// tiles), and its lanes write their pixels together at the end. Measured
+// faster than persistent refilling here, since the tile's rays share lists.
+template <bool OPAQUE, bool COUNT>
+__global__ void __launch_bounds__(kTraceThreads) k_trace_tile(TraceArgs A) {
   const int lane = threadIdx.x & 31;
-  Ray R;
-  if (A.pix_list) {
-    // repair re-trace: warps take 32 queued pixels at a time
-    const uint32_t cnt = min(*A.pix_count, A.pq_cap);
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < cnt;
-         base += warps * 32) {
-      const uint32_t q = base + lane;
-      const bool valid = q < cnt;
-      const uint32_t pix = valid ? A.pix_list[q] : 0u;
-      R.pix = pix;
-      init_ray(A, R, (int)(pix % (uint32_t)A.cam.width), (int)(pix / (uint32_t)A.cam.width), valid);
-      trace_warp<OPAQUE>(A, R);
-      finish(A, R, valid);
-    }
-    return;
-  }
   const int warp = threadIdx.x >> 5;
   const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
   const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
   const bool valid = px < A.cam.width && py < A.cam.height;
+  Ray R;
   R.pix = valid ? (uint32_t)(py * A.cam.width + px) : 0u;
   init_ray(A, R, px, py, valid);
-  trace_warp<OPAQUE>(A, R);
-  finish(A, R, valid);
+  trace_warp<OPAQUE, COUNT>(A, R);
+  finish<COUNT>(A, R, valid);
+}
+
+// Write a finished pixel (or queue it for the repair re-trace).
+__device__ __forceinline__ void write_pixel(const TraceArgs& A, const Ray& R) {
+  if (R.missed) {
+    const uint32_t q = atomicAdd(A.pq_cnt, 1u);
+    if (q < A.pq_cap) A.pq[q] = R.pix;
+    else set_err(A.g.st, kErrOverflow);
+    return;
+  }
+  A.rgba[R.pix] = make_float4(R.C[0], R.C[1], R.C[2], 1.0f - R.T);
+  if (A.first_id) A.first_id[R.pix] = R.first_id;
+  if (A.first_t) A.first_t[R.pix] = R.first_t;
+}
+
+// Opaque and repair traces use persistent warps: a lane whose ray is finished
+// writes its pixel and goes idle; idle lanes take the next work items (one
+// atomic per refill). Work item w of the image is pixel (w mod 32) of the
+// (w / 32)-th 8x4 tile, so a full refill is a coherent tile; in the repair
+// re-trace, item w is the w-th queued pixel.
+template <bool OPAQUE, bool COUNT>
+__global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t W = (uint32_t)A.cam.width, H = (uint32_t)A.cam.height;
+  const uint32_t tiles_x = (W + 7) / 8;
+  const uint32_t total = A.pix_list ? min(*A.pix_count, A.pq_cap) : tiles_x * ((H + 3) / 4) * 32u;
+  Ray R;
+  R.active = R.pending = false;
+  R.n_steps = R.n_entries = R.n_cap = R.n_vox = 0;
+  unsigned c_steps = 0, c_entries = 0, c_cap = 0, c_vox = 0;
+  bool has = false;
+  // Opaque main trace: refill once half the warp is idle. Queued repair
+  // pixels are scattered: a warp takes at most its share of the queue, one
+  // pixel each when few are queued.
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  const int threshold = A.pix_list ? 1 : 16;
+  const int cap = A.pix_list ? (int)min(32u, max(1u, (total + n_warps - 1) / n_warps)) : 32;
+  for (;;) {
+    const unsigned idle = __ballot_sync(FULL, !has);
+    bool exhausted = false;
+    if (__popc(idle) >= threshold) {
+      const int take = min(__popc(idle), cap);
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(A.work_next, (uint32_t)take);
+      base = __shfl_sync(FULL, base, 0);
+      exhausted = base >= total;
+      const int rank = __popc(idle & ((1u << lane) - 1u));
+      if (!has && rank < take) {
+        const uint32_t w = base + (uint32_t)rank;
+        if (w < total) {
+          uint32_t px, py;
+          if (A.pix_list) {
+            const uint32_t pix = A.pix_list[w];
+            px = pix % W;
+            py = pix / W;
+          } else {
+            const uint32_t tile = w >> 5, within = w & 31u;
+            px = (tile % tiles_x) * 8 + (within & 7u);
+            py = (tile / tiles_x) * 4 + (within >> 3);
+          }
+          if (px < W && py < H) {
+            if (COUNT) {
+              c_steps += R.n_steps; c_entries += R.n_entries; c_cap += R.n_cap; c_vox += R.n_vox;
+            }
+            R.pix = py * W + px;
+            init_ray(A, R, (int)px, (int)py, true);
+            has = true;
+          }
+        }
+      }
+    }
+    if (!__any_sync(FULL, has)) {
+      if (__all_sync(FULL, exhausted)) break;
+      continue;
+    }
+    if (has && R.active && !R.pending) {
+      R.pending = advance<COUNT>(A, R);
+      if (!R.pending) R.active = false;
+    }
+    // short lists: every such lane at once, each on its own list
+    if (R.pending && R.end - R.beg <= kShortList) {
+      process_own<OPAQUE, COUNT>(A, R);
+      R.pending = false;
+      if (R.t1 < 0.0f) R.active = false;
+    }
+    // long lists: the whole warp on one list at a time
+    unsigned pm = __ballot_sync(FULL, R.pending);
+    while (pm) {
+      const int L = __ffs(pm) - 1;
+      pm &= pm - 1;
+      process_voxel<OPAQUE, COUNT>(A, R, L);
+      if (lane == L) {
+        R.pending = false;
+        if (R.t1 < 0.0f) R.active = false;
+      }
+    }
+    if (has && !R.active && !R.pending) {
+      write_pixel(A, R);
+      has = false;
+    }
+  }
+  if (COUNT) {
+    unsigned long long e = c_entries + R.n_entries, c = c_cap + R.n_cap, v = c_vox + R.n_vox,
+                       st = c_steps + R.n_steps;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(FULL, e, o);
+      c += __shfl_xor_sync(FULL, c, o);
+      v += __shfl_xor_sync(FULL, v, o);
+      st += __shfl_xor_sync(FULL, st, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.g.st->tr_entries, e);
+      atomicAdd(&A.g.st->tr_capsule, c);
+      atomicAdd(&A.g.st->tr_voxels, v);
+      atomicAdd(&A.g.st->tr_steps, st);
+    }
+  }
+}
+
+// Persistent grid: as many blocks as can be resident at once.
+template <bool OPAQUE, bool COUNT>
+int persistent_blocks(size_t smem) {
+  static int blocks = 0;  // per instantiation; the device does not change under a grid
+  if (!blocks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<OPAQUE, COUNT>, kTraceThreads, smem);
+    blocks = max(1, sms) * max(1, per_sm);
+  }
+  return blocks;
+}
+
+template <bool OPAQUE, bool COUNT>
+void launch_one(const TraceArgs& a, size_t smem, cudaStream_t s) {
+  if (!OPAQUE && !a.pix_list) {
+    const dim3 grid((a.cam.width + 15) / 16, (a.cam.height + 7) / 8);
+    k_trace_tile<OPAQUE, COUNT><<<grid, kTraceThreads, smem, s>>>(a);
+  } else {
+    k_trace<OPAQUE, COUNT><<<persistent_blocks<OPAQUE, COUNT>(smem), kTraceThreads, smem, s>>>(a);
+  }
 }
 
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
-  dim3 grid, block(128);
-  if (a.pix_list) {
-    grid = dim3(152 * 4);  // grid-stride over the queued pixels; cheap when none
+  const size_t smem = K == 1 ? 0 : sizeof(unsigned long long) * kOwnKeys * kTraceThreads;
+  if (a.count) {
+    if (K == 1) launch_one<true, true>(a, smem, s);
+    else launch_one<false, true>(a, smem, s);
   } else {
-    grid = dim3((a.cam.width + 15) / 16, (a.cam.height + 7) / 8);
+    if (K == 1) launch_one<true, false>(a, smem, s);
+    else launch_one<false, false>(a, smem, s);
   }
-  if (K == 1) k_trace<true><<<grid, block, 0, s>>>(a);
-  else k_trace<false><<<grid, block, 0, s>>>(a);
   return 1;
 }
 

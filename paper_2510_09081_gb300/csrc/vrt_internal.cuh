@@ -53,6 +53,13 @@ struct DevStatus {
   unsigned int repair_rounds;
   unsigned int retraced_pixels;
   unsigned int pad_;
+  // trace work counters (only with VRT_OPT_TRACE_COUNTERS)
+  unsigned long long tr_entries;     // list entries examined
+  unsigned long long tr_capsule;     // entries past the line-distance test
+  unsigned long long tr_voxels;      // voxel lists processed
+  unsigned long long tr_steps;       // DDA steps (voxels and empty bricks)
+  unsigned int tr_next[kMaxRepairRounds + 1];  // work items handed out per trace launch
+  unsigned int tr_pad;
 };
 
 // -------------------------------------------------------------- grid layout
