@@ -29,13 +29,14 @@ struct vrt_grid_s {
   float4* pos = nullptr;
   float4* nrm = nullptr;
   // voxels
-  uint32_t *word = nullptr, *cur = nullptr, *vis = nullptr, *visb = nullptr, *occb = nullptr;
-  uint32_t *need = nullptr, *needb = nullptr;
+  uint32_t *word = nullptr, *cur = nullptr, *vis = nullptr, *occb = nullptr;
+  uint32_t* need = nullptr;
   uint8_t* eroded = nullptr;
   uint32_t* lists = nullptr;
   unsigned long long list_cap = 0;
   uint2* xq = nullptr;      // pairs the fp32 filter left to the exact path
   uint32_t xq_cap = 0;
+  unsigned long long* rec = nullptr;  // fragment records of pass 1 (list_cap entries)
   unsigned long long* tile_state = nullptr;
   uint32_t n_tiles = 0;
   float* mips = nullptr;
@@ -103,9 +104,10 @@ GridDev gdev(vrt_grid g) {
   d.corr = (g->r / d.r_clamp) * (g->r / d.r_clamp);
   d.occ_scale = (float)g->occ_scale;
   d.force_exact = g->force_exact;
-  d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.visb = g->visb; d.occb = g->occb;
+  d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.occb = g->occb;
   d.lists = g->lists; d.list_cap = g->list_cap;
   d.xq = g->xq; d.xq_cap = g->xq_cap;
+  d.rec = g->rec; d.rec_cap = (uint32_t)g->list_cap;
   d.st = g->st;
   return d;
 }
@@ -221,9 +223,9 @@ void free_all(vrt_grid g) {
     for (int j = 0; j < 2; ++j)
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
   dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
-  dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->visb); dfree(g->occb);
-  dfree(g->need); dfree(g->needb); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
-  dfree(g->xq);
+  dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->occb);
+  dfree(g->need); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
+  dfree(g->xq); dfree(g->rec);
   dfree(g->mips); dfree(g->vq[0]); dfree(g->vq[1]); dfree(g->pq[0]); dfree(g->pq[1]);
   dfree(g->st);
 }
@@ -263,9 +265,7 @@ vrt_status vrt_create_grid(const vrt_grid_desc* desc, void* cuda_stream, vrt_gri
   chk(dalloc(&g->cur, nv));
   chk(dalloc(&g->vis, nv / 32));
   chk(dalloc(&g->need, nv / 32));
-  chk(dalloc(&g->visb, (nb + 31) / 32));
   chk(dalloc(&g->occb, (nb + 31) / 32));
-  chk(dalloc(&g->needb, (nb + 31) / 32));
   g->n_tiles = (uint32_t)(nv / 4096);
   chk(dalloc(&g->tile_state, g->n_tiles));
   chk(dalloc(&g->st, 1));
@@ -324,18 +324,45 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
     VRT_CUDA(g, dalloc(&g->nrm, (size_t)V + 1));
     g->V_alloc = V;
   }
-  // default capacity: a generous bound on fragments per segment for tubes of
-  // this radius, (2 rl + 2)^2 (2 rl + 3) * 4, at least 24
+  // Default capacity: a tube of length L and list radius rl touches fewer than
+  // (L + 2 rl + 2) (2 rl + 2)^2 voxels; 0.9 of that at the mean segment
+  // length (about 2.5x the fragments measured on the synthetic sets), at
+  // least 16 per vertex.
   const double rl = (double)g->RL / 16384.0;
-  const double per = std::max(24.0, 4.0 * (2 * rl + 2) * (2 * rl + 2) * (2 * rl + 3));
+  double mean_len = 0.0;
+  {
+    std::vector<float> hx;
+    const float* hp = xyz;
+    int hs = stride;
+    if (on_device && V > 0) {
+      hx.resize((size_t)V * 3);
+      VRT_CUDA(g, cudaMemcpy2D(hx.data(), 3 * sizeof(float), xyz, (size_t)stride * sizeof(float),
+                               3 * sizeof(float), (size_t)V, cudaMemcpyDeviceToHost));
+      hp = hx.data();
+      hs = 3;
+    }
+    double sum = 0.0;
+    long long nseg = 0;
+    for (long long i = 0; i + 1 < V; ++i) {
+      if (fl[i] & kLast) continue;
+      const double dx = hp[(i + 1) * hs] - hp[i * hs], dy = hp[(i + 1) * hs + 1] - hp[i * hs + 1],
+                   dz = hp[(i + 1) * hs + 2] - hp[i * hs + 2];
+      sum += std::sqrt(dx * dx + dy * dy + dz * dz);
+      ++nseg;
+    }
+    mean_len = nseg ? sum / (double)nseg : 0.0;
+  }
+  const double per = std::max(16.0, 0.9 * (mean_len + 2 * rl + 2) * (2 * rl + 2) * (2 * rl + 2));
   unsigned long long cap = g->max_frag_desc ? g->max_frag_desc
                                             : (unsigned long long)(per * (double)std::max(V, 1ll));
   cap = std::min<unsigned long long>(cap, 0xffffffffull);
   if (cap != g->list_cap || !g->lists) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
     dfree(g->lists);
+    dfree(g->rec);
     g->list_cap = 0;
     VRT_CUDA(g, dalloc(&g->lists, (size_t)cap));
+    VRT_CUDA(g, dalloc(&g->rec, (size_t)cap));
     g->list_cap = cap;
   }
   {
@@ -413,7 +440,6 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   if (p->cull && !(p->alpha > 0.0f && p->alpha <= 1.0f))
     return fail(g, VRT_ERR_INVALID_ARG, "alpha must be in (0, 1]");
   const size_t nv = (size_t)g->n * g->n * g->n;
-  const size_t nbw = (nv / 64 + 31) / 32;
   const GridDev d = gdev(g);
   // reset the list-build counters (scan tile counter .. end)
   const size_t off = offsetof(DevStatus, sum_count_field);
@@ -423,11 +449,9 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   stage_mark(g, ST_CULL, 0);
   if (p->cull) {
     if (!g->eroded) VRT_CUDA(g, dalloc(&g->eroded, nv));
-    VRT_CUDA(g, cudaMemsetAsync(g->visb, 0, nbw * 4, g->stream));
     g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->stream);
   } else {
     VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
-    VRT_CUDA(g, cudaMemsetAsync(g->visb, 0xff, nbw * 4, g->stream));
   }
   stage_mark(g, ST_CULL, 1);
   stage_mark(g, ST_SCAN, 0);
@@ -435,7 +459,7 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   g->launches += launch_finalize(d, g->stream);
   stage_mark(g, ST_SCAN, 1);
   stage_mark(g, ST_PASS2, 0);
-  g->launches += launch_pass2(g->pos, g->V, d, p->cull ? 1 : 0, nullptr, nullptr, nullptr, g->stream);
+  g->launches += launch_scatter(d, p->cull ? 1 : 0, nullptr, nullptr, g->stream);
   stage_mark(g, ST_PASS2, 1);
   VRT_CUDA(g, cudaGetLastError());
   g->culled = p->cull ? 1 : 0;
@@ -506,15 +530,11 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   if (g->culled) {
     stage_mark(g, ST_REPAIR, 0);
     const GridDev d = gdev(g);
-    const size_t nbw = ((size_t)g->n * g->n * g->n / 64 + 31) / 32;
     for (int r = 0; r < kMaxRepairRounds; ++r) {
       const int ci = r & 1, nx = ci ^ 1;
-      VRT_CUDA(g, cudaMemsetAsync(g->needb, 0, nbw * 4, g->stream));
-      VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, xq_cnt), 0,
-                                  sizeof(unsigned int), g->stream));
-      g->launches += launch_repair_alloc(d, g->needb, g->vq[ci], &g->st->vq_cnt[ci], &g->st->pq_cnt[ci],
+      g->launches += launch_repair_alloc(d, g->vq[ci], &g->st->vq_cnt[ci], &g->st->pq_cnt[ci],
                                          g->vq_cap, g->stream);
-      g->launches += launch_pass2(g->pos, g->V, d, 2, g->need, g->needb, &g->st->vq_cnt[ci], g->stream);
+      g->launches += launch_scatter(d, 2, g->need, &g->st->vq_cnt[ci], g->stream);
       g->launches += launch_repair_clear(d, g->need, g->vq[ci], &g->st->vq_cnt[ci], g->vq_cap, nx, g->stream);
       TraceArgs b = a;
       b.pix_list = g->pq[ci];

@@ -15,8 +15,6 @@
 // stops. The marks decide which voxels get lists; voxels a ray later needs but
 // that were left unmarked are listed by the trace's repair rounds, so the
 // marks only affect speed.
-// A brick bit is set when any voxel of the brick is marked (segment culling
-// in pass 2 tests the segment's box against these bits).
 #include <cmath>
 
 #include "launch.h"
@@ -135,10 +133,7 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
     }
   }
   const uint32_t m = __ballot_sync(0xffffffffu, visible);
-  if ((threadIdx.x & 31) == 0 && idx < nvox) {
-    g.vis[idx >> 5] = m;
-    if (m) atomicOr(&g.visb[idx >> 11], 1u << ((idx >> 6) & 31));
-  }
+  if ((threadIdx.x & 31) == 0 && idx < nvox) g.vis[idx >> 5] = m;
 }
 
 namespace {

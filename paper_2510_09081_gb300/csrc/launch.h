@@ -52,10 +52,11 @@ int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* p
                    DevStatus* st, cudaStream_t s);
 int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,
                   cudaStream_t s);
-// mode 0: every occupied voxel listed; 1: listed voxels from the cull marks;
-// 2: repair (only voxels whose `need` bit is set, bricks from `needb`)
-int launch_pass2(const float4* pos, long long V, const GridDev& g, int mode, const uint32_t* need,
-                  const uint32_t* needb, const uint32_t* pending, cudaStream_t s);
+// Pass 2 over the fragment records. mode 0: every occupied voxel has a list;
+// 1: voxels marked by the cull; 2: repair, only voxels whose `need` bit is set
+// (skipped when *pending is 0).
+int launch_scatter(const GridDev& g, int mode, const uint32_t* need, const uint32_t* pending,
+                   cudaStream_t s);
 int launch_scan(const GridDev& g, int all_visible, unsigned long long* tile_state, uint32_t n_tiles,
                  cudaStream_t s);
 int launch_finalize(const GridDev& g, cudaStream_t s);
@@ -66,9 +67,8 @@ int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* e
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
 // Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
 // them, then clear their `need` bits and the next round's queue counters.
-int launch_repair_alloc(const GridDev& g, uint32_t* needb, const uint32_t* vq,
-                        const uint32_t* vq_cnt, const uint32_t* pq_cnt, uint32_t vq_cap,
-                        cudaStream_t s);
+int launch_repair_alloc(const GridDev& g, const uint32_t* vq, const uint32_t* vq_cnt,
+                        const uint32_t* pq_cnt, uint32_t vq_cap, cudaStream_t s);
 int launch_repair_clear(const GridDev& g, uint32_t* need, const uint32_t* vq,
                          const uint32_t* vq_cnt, uint32_t vq_cap, int next, cudaStream_t s);
 

@@ -771,7 +771,7 @@ int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------- repair
-__global__ void k_repair_alloc(GridDev g, uint32_t* needb, const uint32_t* vq, const uint32_t* vq_cnt,
+__global__ void k_repair_alloc(GridDev g, const uint32_t* vq, const uint32_t* vq_cnt,
                                const uint32_t* pq_cnt, uint32_t vq_cap) {
   const uint32_t nq = min(*vq_cnt, vq_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0 && nq) {
@@ -786,9 +786,6 @@ __global__ void k_repair_alloc(GridDev g, uint32_t* needb, const uint32_t* vq, c
     if ((unsigned long long)start + cnt > g.list_cap) set_err(g.st, kErrOverflow);
     g.cur[idx] = start;
     atomicOr(&g.vis[idx >> 5], 1u << (idx & 31));
-    const uint32_t b = idx >> 6;
-    atomicOr(&g.visb[b >> 5], 1u << (b & 31));
-    atomicOr(&needb[b >> 5], 1u << (b & 31));
   }
 }
 
@@ -805,10 +802,9 @@ __global__ void k_repair_clear(GridDev g, uint32_t* need, const uint32_t* vq, co
   }
 }
 
-int launch_repair_alloc(const GridDev& g, uint32_t* needb, const uint32_t* vq,
-                        const uint32_t* vq_cnt, const uint32_t* pq_cnt, uint32_t vq_cap,
-                        cudaStream_t s) {
-  k_repair_alloc<<<152, 256, 0, s>>>(g, needb, vq, vq_cnt, pq_cnt, vq_cap);
+int launch_repair_alloc(const GridDev& g, const uint32_t* vq, const uint32_t* vq_cnt,
+                        const uint32_t* pq_cnt, uint32_t vq_cap, cudaStream_t s) {
+  k_repair_alloc<<<152, 256, 0, s>>>(g, vq, vq_cnt, pq_cnt, vq_cap);
   return 1;
 }
 

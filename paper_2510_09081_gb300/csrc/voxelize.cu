@@ -19,9 +19,11 @@
 // the 128-bit integer path out of the hot kernels' registers).
 //
 // Pass 1 adds (occupancy code << 16) | 1 to the voxel's packed word with one
-// 32-bit atomic (Sec. 3.1); pass 2 appends the segment id to the lists of
-// voxels that received a list (Sec. 3.3), after skipping segments whose box
-// touches no listed brick.
+// 32-bit atomic (Sec. 3.1) and appends the fragment as an 8-byte record
+// (voxel << 32 | segment), warp-aggregated. The paper re-voxelizes in its
+// second pass to save memory; with the records in HBM the second pass is a
+// streaming scatter instead: for every record whose voxel received a list,
+// bump the voxel's cursor and write the segment id (Sec. 3.3).
 #include "launch.h"
 
 namespace vrt {
@@ -32,6 +34,7 @@ constexpr unsigned FULLW = 0xffffffffu;
 struct Walk {
   float3 a, b;
   float am, a1, a2, s1, s2, rho1, rho2, lo_m, hi_m;
+  float inv_w12, inv_w2;  // reciprocals of W1 * W2 and W2 for the decode
   int m, c0, W1, W2;
   uint32_t n;  // candidates: slabs * W1 * W2
 };
@@ -62,6 +65,8 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
   w.W1 = (int)floorf(fabsf(w.s1) + 2.0f * w.rho1) + 2;
   w.W2 = (int)floorf(fabsf(w.s2) + 2.0f * w.rho2) + 2;
   w.n = c1 >= w.c0 ? (uint32_t)(c1 - w.c0 + 1) * (uint32_t)(w.W1 * w.W2) : 0u;
+  w.inv_w12 = 1.0f / (float)(w.W1 * w.W2);
+  w.inv_w2 = 1.0f / (float)w.W2;
 }
 
 __device__ __forceinline__ Walk shfl_walk(const Walk& w, int src) {
@@ -79,6 +84,8 @@ __device__ __forceinline__ Walk shfl_walk(const Walk& w, int src) {
   r.rho2 = __shfl_sync(FULLW, w.rho2, src);
   r.lo_m = __shfl_sync(FULLW, w.lo_m, src);
   r.hi_m = __shfl_sync(FULLW, w.hi_m, src);
+  r.inv_w12 = __shfl_sync(FULLW, w.inv_w12, src);
+  r.inv_w2 = __shfl_sync(FULLW, w.inv_w2, src);
   r.m = __shfl_sync(FULLW, w.m, src);
   r.c0 = __shfl_sync(FULLW, w.c0, src);
   r.W1 = __shfl_sync(FULLW, w.W1, src);
@@ -90,12 +97,14 @@ __device__ __forceinline__ Walk shfl_walk(const Walk& w, int src) {
 // Candidate q of walk w: its voxel, or false when q falls outside its slab's box.
 __device__ __forceinline__ bool walk_decode(const Walk& w, int n, uint32_t q, int& x, int& y,
                                             int& z) {
-  const uint32_t w12 = (uint32_t)(w.W1 * w.W2);
-  const uint32_t slab = q / w12;
-  const uint32_t rem = q - slab * w12;
-  const int dj = (int)(rem / (uint32_t)w.W2);
-  const int dl = (int)rem - dj * w.W2;
-  const int c = w.c0 + (int)slab;
+  // (q + 1/2) / w is at least 1/(2w) from an integer, far beyond fp32 error for
+  // these small counts, so truncation gives the exact quotient
+  const int w12 = w.W1 * w.W2;
+  const int slab = (int)(((float)q + 0.5f) * w.inv_w12);
+  const int rem = (int)q - slab * w12;
+  const int dj = (int)(((float)rem + 0.5f) * w.inv_w2);
+  const int dl = rem - dj * w.W2;
+  const int c = w.c0 + slab;
   const float x0 = fmaxf((float)c, w.lo_m), x1 = fminf((float)(c + 1), w.hi_m);
   const float p1a = fmaf(x0 - w.am, w.s1, w.a1), p1b = fmaf(x1 - w.am, w.s1, w.a1);
   const float p2a = fmaf(x0 - w.am, w.s2, w.a2), p2b = fmaf(x1 - w.am, w.s2, w.a2);
@@ -145,6 +154,12 @@ __device__ __forceinline__ void add_fragment(const GridDev& g, float3 a, float3 
   sq += q;
 }
 
+__device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, uint32_t seg) {
+  const uint32_t r = atomicAdd(&g.st->rec_cnt, 1u);
+  if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg;
+  else set_err(g.st, kErrOverflow);
+}
+
 __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
                                                const float4* __restrict__ nrm, long long V,
                                                GridDev g) {
@@ -167,6 +182,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     }
   }
   unsigned long long F = 0, sq = 0, ex = 0;
+  const unsigned lt = (1u << lane) - 1u;
   for (int j = 0; j < 32; ++j) {
     if (__shfl_sync(FULLW, w.n, j) == 0) continue;
     const Walk wj = shfl_walk(w, j);
@@ -175,17 +191,34 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     const float3 n1j = make_float3(__shfl_sync(FULLW, n1.x, j), __shfl_sync(FULLW, n1.y, j),
                                    __shfl_sync(FULLW, n1.z, j));
     const uint32_t enj = __shfl_sync(FULLW, en, j);
-    for (uint32_t q = lane; q < wj.n; q += 32) {
-      int x, y, z;
-      if (!walk_decode(wj, g.n, q, x, y, z)) continue;
-      const int dec = g.force_exact ? -1 : seg_filter_at(wj.a, wj.b, x, y, z, g.rl);
-      if (dec == 0) continue;
+    const uint32_t seg = (uint32_t)(base + j);
+    for (uint32_t q0 = 0; q0 < wj.n; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      int x = 0, y = 0, z = 0, dec = 0;
+      if (q < wj.n && walk_decode(wj, g.n, q, x, y, z))
+        dec = g.force_exact ? -1 : seg_filter_at(wj.a, wj.b, x, y, z, g.rl);
       if (dec < 0) {
-        queue_exact(g, (uint32_t)(base + j), x, y, z);
+        queue_exact(g, seg, x, y, z);
         ++ex;
-        continue;
       }
-      add_fragment(g, wj.a, wj.b, n0j, n1j, enj & 1u, enj & 2u, x, y, z, F, sq);
+      uint32_t idx = 0;
+      if (dec > 0) {
+        idx = brick_index(x, y, z, g.log2nb);
+        add_fragment(g, wj.a, wj.b, n0j, n1j, enj & 1u, enj & 2u, x, y, z, F, sq);
+      }
+      // warp-aggregated record append
+      const unsigned am = __ballot_sync(FULLW, dec > 0);
+      if (am) {
+        const int leader = __ffs(am) - 1;
+        uint32_t r0 = 0;
+        if (lane == leader) r0 = atomicAdd(&g.st->rec_cnt, (uint32_t)__popc(am));
+        r0 = __shfl_sync(FULLW, r0, leader);
+        if (dec > 0) {
+          const uint32_t r = r0 + (uint32_t)__popc(am & lt);
+          if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg;
+          else set_err(g.st, kErrOverflow);
+        }
+      }
     }
   }
   flush_counters(g.st, F, sq, ex);
@@ -204,6 +237,7 @@ __global__ void __launch_bounds__(256) k_exact1(const float4* __restrict__ pos,
     if (!seg_exact_at(f3(p0), f3(p1), x, y, z, g.RL)) continue;
     add_fragment(g, f3(p0), f3(p1), f3(nrm[it.x]), f3(nrm[it.x + 1]),
                  __float_as_uint(p0.w) & kClipOn, __float_as_uint(p1.w) & kClipOn, x, y, z, F, sq);
+    append_record(g, brick_index(x, y, z, g.log2nb), it.x);
   }
   unsigned long long z0 = 0;
   flush_counters(g.st, F, sq, z0);
@@ -213,112 +247,30 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t i) {
   return (bits[i >> 5] >> (i & 31)) & 1u;
 }
 
-// Does the box [lo, hi] (voxel coords, clamped) touch a brick whose bit is set?
-__device__ __forceinline__ bool any_brick(const uint32_t* bits, int log2nb, int x0, int y0, int z0,
-                                          int x1, int y1, int z1) {
-  for (int bz = z0 >> 2; bz <= (z1 >> 2); ++bz)
-    for (int by = y0 >> 2; by <= (y1 >> 2); ++by)
-      for (int bx = x0 >> 2; bx <= (x1 >> 2); ++bx) {
-        const uint32_t b = ((uint32_t)bz << (2 * log2nb)) | ((uint32_t)by << log2nb) | (uint32_t)bx;
-        if (bit_set(bits, b)) return true;
-      }
-  return false;
-}
-
-__device__ __forceinline__ void list_append(const GridDev& g, uint32_t idx, uint32_t seg,
-                                            unsigned long long& listed) {
-  const uint32_t slot = atomicAdd(&g.cur[idx], 1u);
-  if (slot < g.list_cap) {
-    g.lists[slot] = seg;
-    ++listed;
-  } else {
-    set_err(g.st, kErrOverflow);
-  }
-}
-
-__device__ __forceinline__ void flush_listed(DevStatus* st, unsigned long long listed,
-                                             unsigned long long ex) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    listed += __shfl_down_sync(FULLW, listed, o);
-    ex += __shfl_down_sync(FULLW, ex, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (listed) atomicAdd(&st->listed, listed);
-    if (ex) atomicAdd(&st->exact_decisions, ex);
-  }
-}
-
-// mode 0: every occupied voxel has a list; 1: voxels marked by the cull;
-// 2: repair -- only voxels whose `need` bit is set (bricks from `needb`).
-__global__ void __launch_bounds__(256) k_pass2(const float4* __restrict__ pos, long long V, GridDev g,
-                                               int mode, const uint32_t* __restrict__ need,
-                                               const uint32_t* __restrict__ needb,
-                                               const uint32_t* __restrict__ pending) {
+// Pass 2: stream the fragment records; mode 0 lists every fragment, mode 1
+// those whose voxel the cull marked, mode 2 (repair) those whose voxel's
+// `need` bit is set.
+__global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint32_t* __restrict__ need,
+                                                 const uint32_t* __restrict__ pending) {
   if (mode == 2 && *pending == 0) return;
-  const int lane = threadIdx.x & 31;
+  const uint32_t cnt = min(g.st->rec_cnt, g.rec_cap);
   const uint32_t* sel = mode == 2 ? need : g.vis;
-  const uint32_t* bb = mode == 1 ? g.visb : needb;
-  const long long stride = (long long)gridDim.x * (blockDim.x >> 5) * 32;
-  unsigned long long ex = 0, listed = 0;
-  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-       base + 1 < V; base += stride) {
-    const long long i = base + lane;
-    Walk w;
-    w.n = 0;
-    if (i + 1 < V) {
-      const float4 p0 = pos[i];
-      if (!(__float_as_uint(p0.w) & kLast)) {
-        const float3 a = f3(p0), b = f3(pos[i + 1]);
-        bool keep = true;
-        if (mode != 0) {
-          const int n = g.n;
-          const int x0 = max(0, (int)floorf(fminf(a.x, b.x) - g.rl - kWalkEps));
-          const int y0 = max(0, (int)floorf(fminf(a.y, b.y) - g.rl - kWalkEps));
-          const int z0 = max(0, (int)floorf(fminf(a.z, b.z) - g.rl - kWalkEps));
-          const int x1 = min(n - 1, (int)floorf(fmaxf(a.x, b.x) + g.rl + kWalkEps));
-          const int y1 = min(n - 1, (int)floorf(fmaxf(a.y, b.y) + g.rl + kWalkEps));
-          const int z1 = min(n - 1, (int)floorf(fmaxf(a.z, b.z) + g.rl + kWalkEps));
-          keep = x0 <= x1 && y0 <= y1 && z0 <= z1 && any_brick(bb, g.log2nb, x0, y0, z0, x1, y1, z1);
-        }
-        if (keep) walk_setup(a, b, g, w);
-      }
-    }
-    for (int j = 0; j < 32; ++j) {
-      if (__shfl_sync(FULLW, w.n, j) == 0) continue;
-      const Walk wj = shfl_walk(w, j);
-      for (uint32_t q = lane; q < wj.n; q += 32) {
-        int x, y, z;
-        if (!walk_decode(wj, g.n, q, x, y, z)) continue;
-        const uint32_t idx = brick_index(x, y, z, g.log2nb);
-        if (!bit_set(sel, idx)) continue;
-        const int dec = g.force_exact ? -1 : seg_filter_at(wj.a, wj.b, x, y, z, g.rl);
-        if (dec == 0) continue;
-        if (dec < 0) {
-          queue_exact(g, (uint32_t)(base + j), x, y, z);
-          ++ex;
-          continue;
-        }
-        list_append(g, idx, (uint32_t)(base + j), listed);
-      }
-    }
-  }
-  flush_listed(g.st, listed, ex);
-}
-
-// Exact decisions of pass 2's undecided pairs (already restricted to voxels
-// that get lists).
-__global__ void __launch_bounds__(256) k_exact2(const float4* __restrict__ pos, GridDev g) {
-  const uint32_t cnt = min(g.st->xq_cnt, g.xq_cap);
-  unsigned long long listed = 0, z0 = 0;
+  unsigned long long listed = 0;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-    const uint2 it = g.xq[e];
-    int x, y, z;
-    unpack_voxel(it.y, x, y, z);
-    if (!seg_exact_at(f3(pos[it.x]), f3(pos[it.x + 1]), x, y, z, g.RL)) continue;
-    list_append(g, brick_index(x, y, z, g.log2nb), it.x, listed);
+    const unsigned long long r = __ldcs(&g.rec[e]);
+    const uint32_t idx = (uint32_t)(r >> 32);
+    if (mode != 0 && !bit_set(sel, idx)) continue;
+    const uint32_t slot = atomicAdd(&g.cur[idx], 1u);
+    if (slot < g.list_cap) {
+      g.lists[slot] = (uint32_t)r;
+      ++listed;
+    } else {
+      set_err(g.st, kErrOverflow);
+    }
   }
-  flush_listed(g.st, listed, z0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) listed += __shfl_down_sync(FULLW, listed, o);
+  if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g.st->listed, listed);
 }
 
 int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,
@@ -330,15 +282,10 @@ int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDe
   return 2;
 }
 
-int launch_pass2(const float4* pos, long long V, const GridDev& g, int mode, const uint32_t* need,
-                 const uint32_t* needb, const uint32_t* pending, cudaStream_t s) {
-  if (V < 2) return 0;
-  const int T = 256;
-  long long blocks = (V - 1 + T - 1) / T;
-  if (mode == 2 && blocks > 152 * 8) blocks = 152 * 8;  // repair: grid-stride, cheap when idle
-  k_pass2<<<(unsigned)blocks, T, 0, s>>>(pos, V, g, mode, need, needb, pending);
-  k_exact2<<<152 * 4, T, 0, s>>>(pos, g);
-  return 2;
+int launch_scatter(const GridDev& g, int mode, const uint32_t* need, const uint32_t* pending,
+                   cudaStream_t s) {
+  k_scatter<<<152 * 8, 256, 0, s>>>(g, mode, need, pending);
+  return 1;
 }
 
 }  // namespace vrt

@@ -37,6 +37,8 @@ struct DevStatus {
   unsigned long long F;              // fragments of pass 1
   unsigned long long sum_q;          // occupancy codes of pass 1
   unsigned long long exact_decisions;  // list decisions on the exact path
+  unsigned int rec_cnt;              // fragment records appended by pass 1
+  unsigned int rec_pad;
   // --- reset by every list build from here on
   unsigned long long sum_count_field;  // checked by the scan
   unsigned long long sum_occ_field;
@@ -83,12 +85,13 @@ struct GridDev {
   uint32_t* word;          // [n^3] packed (occupancy code sum << 16) | count
   uint32_t* cur;           // [n^3] list end cursor (start = cur - count)
   uint32_t* vis;           // [n^3 / 32] voxel has a list
-  uint32_t* visb;          // [bricks / 32] brick has a listed voxel
   uint32_t* occb;          // [bricks / 32] brick has an occupied voxel
   uint32_t* lists;         // [list_cap]
   unsigned long long list_cap;
   uint2* xq;               // [xq_cap] undecided (segment id, packed voxel) pairs
   uint32_t xq_cap;
+  unsigned long long* rec; // [rec_cap] fragment records: voxel << 32 | segment
+  uint32_t rec_cap;
   DevStatus* st;
 };
 
@@ -107,9 +110,12 @@ __device__ __forceinline__ float cmp3(float3 a, int k) { return k == 0 ? a.x : (
 // voxel units relative to the box's lower corner (exact fp32 multiples of
 // 2^-14). Returns 1 (within), 0 (not within) or -1 (too close to call in fp32).
 //
-// Stage 1 uses the box's inscribed and circumscribed balls around the centre c:
-//   dist(seg, c) <= rl + 1/2        -> within
-//   dist(seg, c) >  rl + sqrt(3)/2  -> not within
+// Stage 1 takes the point p of the segment nearest the box centre c, w = p - c:
+//   dist(p, box) <= rl                       -> within (p is on the segment)
+//   |w| - (|w_x| + |w_y| + |w_z|) / (2 |w|)  > rl -> not within: the plane
+//     through p with normal w / |w| has the whole segment on one side (p is
+//     the nearest point of a convex set) and the box, whose support along that
+//     normal is half the 1-norm, on the other.
 // Stage 2 runs Newton steps on the convex, C^1, piecewise-quadratic squared
 // box distance f(t) and brackets its minimum: f(t) is an upper bound, and
 // convexity gives f(t) - |f'(t)| * (t or 1 - t) as a lower bound.
@@ -123,11 +129,17 @@ __device__ __forceinline__ int seg_box_filter(float3 a, float3 d, float rl) {
   const float3 w = make_float3(0.5f - a.x, 0.5f - a.y, 0.5f - a.z);
   float t = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, dot3(w, d) / dd)) : 0.0f;
   {
-    const float3 e = w - t * d;
-    const float dc2 = dot3(e, e);
-    const float in_r = rl + 0.5f, out_r = rl + 0.8660254f;
-    if (dc2 + tol <= in_r * in_r) return 1;
-    if (dc2 - tol > out_r * out_r) return 0;
+    const float3 e = w - t * d;  // c - p
+    const float ex = fmaxf(fabsf(e.x) - 0.5f, 0.0f), ey = fmaxf(fabsf(e.y) - 0.5f, 0.0f),
+                ez = fmaxf(fabsf(e.z) - 0.5f, 0.0f);
+    const float up2 = ex * ex + ey * ey + ez * ez;  // dist(p, box)^2
+    if (up2 + tol <= rl * rl) return 1;
+    const float e2 = dot3(e, e);
+    if (e2 > 0.0f) {
+      const float len = sqrtf(e2);
+      const float lb = len - 0.5f * (fabsf(e.x) + fabsf(e.y) + fabsf(e.z)) / len;
+      if (lb > rl && lb * lb - tol > rl * rl) return 0;
+    }
   }
   float f = 0.0f, g = 0.0f;
 #pragma unroll
