@@ -524,6 +524,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, tr_next), 0,
                               sizeof(unsigned int) * (kMaxRepairRounds + 1), g->stream));
   a.work_next = &g->st->tr_next[0];
+  a.short_list = kShortList;
   stage_mark(g, ST_TRACE, 0);
   g->launches += launch_trace(a, K, g->stream);
   stage_mark(g, ST_TRACE, 1);
@@ -543,6 +544,8 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
       b.pq = g->pq[nx]; b.pq_cnt = &g->st->pq_cnt[nx];
       b.max_queue = (r + 2 >= kMaxRepairRounds) ? 0xffffffffu : kRayQueueLimit;
       b.work_next = &g->st->tr_next[r + 1];
+      // re-traced rays are few and scattered: each list is split over a warp
+      b.short_list = 0;
       g->launches += launch_trace(b, K, g->stream);
     }
     stage_mark(g, ST_REPAIR, 1);

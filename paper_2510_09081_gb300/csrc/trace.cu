@@ -43,7 +43,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
 constexpr int kOwnKeys = 32;              // transparent, own list: keys kept per scan (shared memory)
 constexpr int kTraceThreads = 128;
-constexpr uint32_t kShortList = 64;       // lists up to this length are processed by their own lane
 constexpr float kConeTan = 1.1180340f;    // tan(half angle), cos(half angle) = 2/3
 constexpr int kConeSteps = 4;             // samples per cone: t = 1, 2.118, 4.486, 9.502 (<= 16)
 
@@ -550,7 +549,7 @@ __device__ void trace_warp(const TraceArgs& A, Ray& R) {
     }
     if (!__any_sync(FULL, R.pending)) break;
     // short lists: every such lane at once, each on its own list
-    if (R.pending && R.end - R.beg <= kShortList) {
+    if (R.pending && R.end - R.beg <= A.short_list) {
       process_own<OPAQUE, COUNT>(A, R);
       R.pending = false;
       if (R.t1 < 0.0f) R.active = false;
@@ -694,7 +693,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
       if (!R.pending) R.active = false;
     }
     // short lists: every such lane at once, each on its own list
-    if (R.pending && R.end - R.beg <= kShortList) {
+    if (R.pending && R.end - R.beg <= A.short_list) {
       process_own<OPAQUE, COUNT>(A, R);
       R.pending = false;
       if (R.t1 < 0.0f) R.active = false;

@@ -160,6 +160,23 @@ __device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, ui
   else set_err(g.st, kErrOverflow);
 }
 
+constexpr int kWarpRecords = 256;  // records a warp stages before one global append
+
+// Append a warp's staged records with one atomic (all lanes call).
+__device__ __forceinline__ void flush_records(const GridDev& g, const unsigned long long* srec, int n,
+                                              int lane) {
+  if (n == 0) return;
+  uint32_t r0 = 0;
+  if (lane == 0) r0 = atomicAdd(&g.st->rec_cnt, (uint32_t)n);
+  r0 = __shfl_sync(FULLW, r0, 0);
+  for (int k = lane; k < n; k += 32) {
+    const uint32_t r = r0 + (uint32_t)k;
+    if (r < g.rec_cap) g.rec[r] = srec[k];
+    else set_err(g.st, kErrOverflow);
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
                                                const float4* __restrict__ nrm, long long V,
                                                GridDev g) {
@@ -183,6 +200,9 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   }
   unsigned long long F = 0, sq = 0, ex = 0;
   const unsigned lt = (1u << lane) - 1u;
+  __shared__ unsigned long long s_rec[8][kWarpRecords];
+  unsigned long long* srec = s_rec[threadIdx.x >> 5];
+  int wcount = 0;  // records staged by this warp (uniform)
   for (int j = 0; j < 32; ++j) {
     if (__shfl_sync(FULLW, w.n, j) == 0) continue;
     const Walk wj = shfl_walk(w, j);
@@ -206,21 +226,19 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
         idx = brick_index(x, y, z, g.log2nb);
         add_fragment(g, wj.a, wj.b, n0j, n1j, enj & 1u, enj & 2u, x, y, z, F, sq);
       }
-      // warp-aggregated record append
+      // stage the warp's records in shared memory; one global append per batch
       const unsigned am = __ballot_sync(FULLW, dec > 0);
-      if (am) {
-        const int leader = __ffs(am) - 1;
-        uint32_t r0 = 0;
-        if (lane == leader) r0 = atomicAdd(&g.st->rec_cnt, (uint32_t)__popc(am));
-        r0 = __shfl_sync(FULLW, r0, leader);
-        if (dec > 0) {
-          const uint32_t r = r0 + (uint32_t)__popc(am & lt);
-          if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg;
-          else set_err(g.st, kErrOverflow);
-        }
+      if (dec > 0) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg;
+      wcount += __popc(am);
+      if (wcount > kWarpRecords - 32) {
+        __syncwarp();
+        flush_records(g, srec, wcount, lane);
+        wcount = 0;
       }
     }
   }
+  __syncwarp();
+  flush_records(g, srec, wcount, lane);
   flush_counters(g.st, F, sq, ex);
 }
 
