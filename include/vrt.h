@@ -62,9 +62,13 @@ typedef struct {
   float r_min;            /* PWAA radius clamp of Alg. 3; <= 0 selects 0.5 */
   int32_t occ_scale;      /* occupancy codes per unit occupancy in the packed
                              word; 0 selects 32 */
-  uint64_t max_fragments; /* list capacity in entries (all voxels); 0 selects
-                             4 (2 rl + 2)^2 (2 rl + 3), at least 24, entries
-                             per uploaded vertex, rl = radius + 2^-9 */
+  uint64_t max_fragments; /* list capacity in entries (all voxels), also the
+                             capacity of the fragment record buffer; 0 selects
+                             0.9 (L + 2 rl + 2)(2 rl + 2)^2, at least 16,
+                             entries per uploaded vertex, with L the mean
+                             segment length of the vrt_upload_segments call
+                             and rl = radius + 2^-9; at most 2^32 - 1;
+                             exceeding it reports VRT_ERR_OVERFLOW */
 } vrt_grid_desc;
 
 /* Pinhole or orthographic camera. Basis: f = normalize(target - eye),

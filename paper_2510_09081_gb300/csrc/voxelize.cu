@@ -12,9 +12,9 @@
 // |d_ai / d_a0| + 2 * half-extent), so candidate q of a segment decodes in O(1).
 //
 // Work layout: each lane loads one segment (coalesced) and sets up its walk;
-// the warp then takes its 32 segments one at a time and splits the current
-// segment's candidates over the lanes, so segments of different lengths do not
-// leave lanes idle. The fp32 filter decides almost every candidate; pairs it
+// the warp numbers the candidates of its 32 segments consecutively and takes
+// them 32 at a time, each lane pulling its segment's walk by shuffles, so
+// segments of different lengths do not leave lanes idle. The fp32 filter decides almost every candidate; pairs it
 // cannot decide go to a queue that a separate kernel decides exactly (keeping
 // the 128-bit integer path out of the hot kernels' registers).
 //
@@ -39,6 +39,18 @@ struct Walk {
   uint32_t n;  // candidates: slabs * W1 * W2
 };
 
+// Minor-axis voxel ranges of slab c (clamped to the grid).
+__device__ __forceinline__ void slab_box(const Walk& w, int n, int c, int& j0, int& j1, int& l0,
+                                         int& l1) {
+  const float x0 = fmaxf((float)c, w.lo_m), x1 = fminf((float)(c + 1), w.hi_m);
+  const float p1a = fmaf(x0 - w.am, w.s1, w.a1), p1b = fmaf(x1 - w.am, w.s1, w.a1);
+  const float p2a = fmaf(x0 - w.am, w.s2, w.a2), p2b = fmaf(x1 - w.am, w.s2, w.a2);
+  j0 = max(0, (int)floorf(fminf(p1a, p1b) - w.rho1));
+  j1 = min(n - 1, (int)floorf(fmaxf(p1a, p1b) + w.rho1));
+  l0 = max(0, (int)floorf(fminf(p2a, p2b) - w.rho2));
+  l1 = min(n - 1, (int)floorf(fmaxf(p2a, p2b) + w.rho2));
+}
+
 __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g, Walk& w) {
   const float rl = g.rl;
   const int n = g.n;
@@ -61,9 +73,16 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
   w.a2 = cmp3(a, k2);
   w.c0 = max(0, (int)floorf(w.lo_m - kWalkEps));
   const int c1 = min(n - 1, (int)floorf(w.hi_m + kWalkEps));
-  // a range of length L touches at most floor(L) + 2 unit cells
-  w.W1 = (int)floorf(fabsf(w.s1) + 2.0f * w.rho1) + 2;
-  w.W2 = (int)floorf(fabsf(w.s2) + 2.0f * w.rho2) + 2;
+  // index every slab's box with the widest slab's widths
+  int W1 = 1, W2 = 1;
+  for (int c = w.c0; c <= c1; ++c) {
+    int j0, j1, l0, l1;
+    slab_box(w, n, c, j0, j1, l0, l1);
+    W1 = max(W1, j1 - j0 + 1);
+    W2 = max(W2, l1 - l0 + 1);
+  }
+  w.W1 = W1;
+  w.W2 = W2;
   w.n = c1 >= w.c0 ? (uint32_t)(c1 - w.c0 + 1) * (uint32_t)(w.W1 * w.W2) : 0u;
   w.inv_w12 = 1.0f / (float)(w.W1 * w.W2);
   w.inv_w2 = 1.0f / (float)w.W2;
@@ -105,13 +124,8 @@ __device__ __forceinline__ bool walk_decode(const Walk& w, int n, uint32_t q, in
   const int dj = (int)(((float)rem + 0.5f) * w.inv_w2);
   const int dl = rem - dj * w.W2;
   const int c = w.c0 + slab;
-  const float x0 = fmaxf((float)c, w.lo_m), x1 = fminf((float)(c + 1), w.hi_m);
-  const float p1a = fmaf(x0 - w.am, w.s1, w.a1), p1b = fmaf(x1 - w.am, w.s1, w.a1);
-  const float p2a = fmaf(x0 - w.am, w.s2, w.a2), p2b = fmaf(x1 - w.am, w.s2, w.a2);
-  const int j0 = max(0, (int)floorf(fminf(p1a, p1b) - w.rho1));
-  const int j1 = min(n - 1, (int)floorf(fmaxf(p1a, p1b) + w.rho1));
-  const int l0 = max(0, (int)floorf(fminf(p2a, p2b) - w.rho2));
-  const int l1 = min(n - 1, (int)floorf(fmaxf(p2a, p2b) + w.rho2));
+  int j0, j1, l0, l1;
+  slab_box(w, n, c, j0, j1, l0, l1);
   const int j = j0 + dj, l = l0 + dl;
   if (j > j1 || l > l1) return false;
   const int m = w.m;
@@ -203,38 +217,51 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   __shared__ unsigned long long s_rec[8][kWarpRecords];
   unsigned long long* srec = s_rec[threadIdx.x >> 5];
   int wcount = 0;  // records staged by this warp (uniform)
-  for (int j = 0; j < 32; ++j) {
-    if (__shfl_sync(FULLW, w.n, j) == 0) continue;
+  // The warp's candidates, segment after segment, are numbered 0..total-1;
+  // lane l takes number t0 + l and finds its segment by a binary search over
+  // the inclusive prefix of the candidate counts.
+  uint32_t incl = w.n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(FULLW, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t total = __shfl_sync(FULLW, incl, 31);
+  for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+    const uint32_t gq = t0 + lane;
+    int j = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+      if (__shfl_sync(FULLW, incl, j + st - 1) <= gq) j += st;
+    j = min(j, 31);
     const Walk wj = shfl_walk(w, j);
     const float3 n0j = make_float3(__shfl_sync(FULLW, n0.x, j), __shfl_sync(FULLW, n0.y, j),
                                    __shfl_sync(FULLW, n0.z, j));
     const float3 n1j = make_float3(__shfl_sync(FULLW, n1.x, j), __shfl_sync(FULLW, n1.y, j),
                                    __shfl_sync(FULLW, n1.z, j));
     const uint32_t enj = __shfl_sync(FULLW, en, j);
+    const uint32_t q = gq - (__shfl_sync(FULLW, incl, j) - wj.n);
     const uint32_t seg = (uint32_t)(base + j);
-    for (uint32_t q0 = 0; q0 < wj.n; q0 += 32) {
-      const uint32_t q = q0 + lane;
-      int x = 0, y = 0, z = 0, dec = 0;
-      if (q < wj.n && walk_decode(wj, g.n, q, x, y, z))
-        dec = g.force_exact ? -1 : seg_filter_at(wj.a, wj.b, x, y, z, g.rl);
-      if (dec < 0) {
-        queue_exact(g, seg, x, y, z);
-        ++ex;
-      }
-      uint32_t idx = 0;
-      if (dec > 0) {
-        idx = brick_index(x, y, z, g.log2nb);
-        add_fragment(g, wj.a, wj.b, n0j, n1j, enj & 1u, enj & 2u, x, y, z, F, sq);
-      }
-      // stage the warp's records in shared memory; one global append per batch
-      const unsigned am = __ballot_sync(FULLW, dec > 0);
-      if (dec > 0) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg;
-      wcount += __popc(am);
-      if (wcount > kWarpRecords - 32) {
-        __syncwarp();
-        flush_records(g, srec, wcount, lane);
-        wcount = 0;
-      }
+    int x = 0, y = 0, z = 0, dec = 0;
+    if (gq < total && walk_decode(wj, g.n, q, x, y, z))
+      dec = g.force_exact ? -1 : seg_filter_at(wj.a, wj.b, x, y, z, g.rl);
+    if (dec < 0) {
+      queue_exact(g, seg, x, y, z);
+      ++ex;
+    }
+    uint32_t idx = 0;
+    if (dec > 0) {
+      idx = brick_index(x, y, z, g.log2nb);
+      add_fragment(g, wj.a, wj.b, n0j, n1j, enj & 1u, enj & 2u, x, y, z, F, sq);
+    }
+    // stage the warp's records in shared memory; one global append per batch
+    const unsigned am = __ballot_sync(FULLW, dec > 0);
+    if (dec > 0) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg;
+    wcount += __popc(am);
+    if (wcount > kWarpRecords - 32) {
+      __syncwarp();
+      flush_records(g, srec, wcount, lane);
+      wcount = 0;
     }
   }
   __syncwarp();
