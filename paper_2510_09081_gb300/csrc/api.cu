@@ -544,8 +544,6 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
       b.pq = g->pq[nx]; b.pq_cnt = &g->st->pq_cnt[nx];
       b.max_queue = (r + 2 >= kMaxRepairRounds) ? 0xffffffffu : kRayQueueLimit;
       b.work_next = &g->st->tr_next[r + 1];
-      // re-traced rays are few and scattered: each list is split over a warp
-      b.short_list = 0;
       g->launches += launch_trace(b, K, g->stream);
     }
     stage_mark(g, ST_REPAIR, 1);

@@ -45,7 +45,7 @@ struct TraceArgs {
   uint32_t vq_cap, pq_cap;
   uint32_t max_queue;        // culled voxels one ray may queue before it stops
   uint32_t* work_next;       // next work item (persistent warps)
-  uint32_t short_list;       // lists up to this length go to their own lane
+  uint32_t short_list;       // lists up to this length share the warp entry by entry
   int count;                 // accumulate trace work counters
 };
 

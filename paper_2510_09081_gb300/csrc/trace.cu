@@ -4,9 +4,11 @@
 // queued pixels). Each lane steps its own ray by 3D-DDA (Amanatides & Woo)
 // through the grid box, crossing bricks with no occupied voxel in one step
 // (empty-space skipping), until it reaches a voxel with a list. The warp then
-// processes the pending voxels of its lanes one at a time, all 32 lanes
-// splitting that voxel's list (lane l takes entries l, l+32, ...), so a long
-// list costs len/32 steps and no lane idles on another lane's list.
+// numbers the entries of all its lanes' pending lists one after another and
+// takes them 32 at a time, one (ray, entry) pair per lane, so no lane idles on
+// another lane's longer list. Very long lists, and a transparent ray with more
+// hits in one voxel than its shared-memory slots hold, go to a whole-warp path
+// that processes one voxel at a time (lane l takes entries l, l+32, ...).
 //
 // For each listed segment the lane computes the first entry of the ray into
 // the segment's capsule; an entry counts only if it lies in the voxel's ray
@@ -14,9 +16,11 @@
 // is counted once and hits come out voxel by voxel in depth order -- and both
 // clip planes keep it. A cheap line-to-line distance test skips segments whose
 // line passes farther than r from the ray.
-//  - opaque: the warp's minimum 64-bit key (depth bits << 32 | segment id) is
-//    the voxel's nearest hit; the ray stops at the first voxel that has one.
-//  - transparent: each lane keeps its 4 smallest keys beyond the last
+//  - opaque: the minimum 64-bit key (depth bits << 32 | segment id) is the
+//    voxel's nearest hit; the ray stops at the first voxel that has one.
+//  - transparent, shared entries: a ray's hits in the voxel are collected in
+//    shared memory, sorted by key and composited by the ray's lane.
+//  - transparent, whole-warp path: each lane keeps its 4 smallest keys beyond the last
 //    composited one; the warp extracts keys in global (depth, id) order by
 //    repeated minimum reductions -- only up to the smallest key a lane had to
 //    drop, beyond which it rescans the list -- shades up to 32 of them in
@@ -539,6 +543,126 @@ __device__ void process_own(const TraceArgs& A, Ray& R) {
   if (COUNT) R.n_cap += n_cap;
 }
 
+// The pending voxels of the warp's lanes with lists up to A.short_list
+// entries, processed together: their entries are numbered one after another
+// (lane by lane) and the warp takes 32 at a time, one (ray, entry) pair per
+// lane, so lanes with short lists do not wait for the longest one. A hit goes
+// to its ray's slots in shared memory (the nearest key for an opaque ray; up to
+// kOwnKeys keys of a transparent ray, sorted and composited by the ray's own
+// lane afterwards). A transparent ray with more hits in the voxel keeps its
+// voxel pending for the whole-warp path, which starts it again from scratch.
+template <bool OPAQUE, bool COUNT>
+__device__ void process_flat(const TraceArgs& A, Ray& R) {
+  extern __shared__ unsigned long long s_key[];  // [kOwnKeys][kTraceThreads]
+  __shared__ float4 s_ray[2][kTraceThreads];      // (o, t_enter), (d, t_exit)
+  __shared__ uint32_t s_cnt[kTraceThreads];
+  __shared__ unsigned long long s_best[kTraceThreads];
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, wb = tid & ~31;
+  const bool take = R.pending && R.end - R.beg <= A.short_list;
+  const uint32_t len = take ? R.end - R.beg : 0u;
+  uint32_t incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  if (total == 0) return;
+  if (take) {
+    s_ray[0][tid] = make_float4(R.o.x, R.o.y, R.o.z, R.vt0);
+    s_ray[1][tid] = make_float4(R.d.x, R.d.y, R.d.z, R.vt1);
+  }
+  if (OPAQUE) s_best[tid] = ~0ull;
+  else s_cnt[tid] = 0u;
+  __syncwarp();
+  const uint32_t first = R.beg - (incl - len);  // entry g of this lane is lists[first + g]
+  const float r2 = A.g.r * A.g.r;
+  const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
+  unsigned n_cap = 0;
+  for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+    const uint32_t gq = t0 + lane;
+    int j = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+      if (__shfl_sync(FULL, incl, j + st - 1) <= gq) j += st;
+    j = min(j, 31);
+    const uint32_t fj = __shfl_sync(FULL, first, j);
+    if (gq < total) {
+      const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
+      const unsigned long long k =
+          entry_key<COUNT>(A, fj + gq, f3(ro), f3(rd), ro.w, rd.w, r2, rrm, n_cap);
+      if (k != ~0ull) {
+        if (OPAQUE) {
+          atomicMin(&s_best[wb + j], k);
+        } else {
+          const uint32_t slot = atomicAdd(&s_cnt[wb + j], 1u);
+          if (slot < (uint32_t)kOwnKeys) s_key[slot * kTraceThreads + wb + j] = k;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (COUNT) R.n_cap += n_cap;
+  if (!take) return;
+  if (OPAQUE) {
+    if (COUNT) {
+      ++R.n_vox;
+      R.n_entries += len;
+    }
+    const unsigned long long best = s_best[tid];
+    if (best != ~0ull) {
+      const uint32_t id = (uint32_t)(best & 0xffffffffu);
+      const float t = __uint_as_float((uint32_t)(best >> 32));
+      float3 c = tangent_colour(A, id);
+      if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
+      R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
+      R.T *= (1.0f - A.alpha);
+      R.first_id = (int)id;
+      R.first_t = t;
+      R.active = false;
+    }
+    R.pending = false;
+    if (R.t1 < 0.0f) R.active = false;
+    return;
+  }
+  const uint32_t nk = s_cnt[tid];
+  if (nk > (uint32_t)kOwnKeys) return;  // stays pending: the whole-warp path redoes it
+  if (COUNT) {
+    ++R.n_vox;
+    R.n_entries += len;
+  }
+  unsigned long long* kb = s_key + tid;
+  for (uint32_t q = 1; q < nk; ++q) {
+    const unsigned long long k = kb[q * kTraceThreads];
+    uint32_t p = q;
+    while (p > 0 && kb[(p - 1) * kTraceThreads] > k) {
+      kb[p * kTraceThreads] = kb[(p - 1) * kTraceThreads];
+      --p;
+    }
+    kb[p * kTraceThreads] = k;
+  }
+  const float om = 1.0f - A.alpha;
+  for (uint32_t q = 0; q < nk && R.T >= kTStop; ++q) {
+    const unsigned long long kq = kb[q * kTraceThreads];
+    const uint32_t id = (uint32_t)(kq & 0xffffffffu);
+    const float t = __uint_as_float((uint32_t)(kq >> 32));
+    float3 c = tangent_colour(A, id);
+    if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
+    const float w = R.T * A.alpha;
+    R.C[0] = fmaf(w, c.x, R.C[0]);
+    R.C[1] = fmaf(w, c.y, R.C[1]);
+    R.C[2] = fmaf(w, c.z, R.C[2]);
+    R.T *= om;
+    if (R.first_id < 0) {
+      R.first_id = (int)id;
+      R.first_t = t;
+    }
+  }
+  R.pending = false;
+  if (R.T < kTStop || R.t1 < 0.0f) R.active = false;
+}
+
 template <bool OPAQUE, bool COUNT>
 __device__ void trace_warp(const TraceArgs& A, Ray& R) {
   const int lane = threadIdx.x & 31;
@@ -548,12 +672,7 @@ __device__ void trace_warp(const TraceArgs& A, Ray& R) {
       if (!R.pending) R.active = false;
     }
     if (!__any_sync(FULL, R.pending)) break;
-    // short lists: every such lane at once, each on its own list
-    if (R.pending && R.end - R.beg <= A.short_list) {
-      process_own<OPAQUE, COUNT>(A, R);
-      R.pending = false;
-      if (R.t1 < 0.0f) R.active = false;
-    }
+    process_flat<OPAQUE, COUNT>(A, R);
     // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
     while (pm) {
@@ -692,12 +811,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
       R.pending = advance<COUNT>(A, R);
       if (!R.pending) R.active = false;
     }
-    // short lists: every such lane at once, each on its own list
-    if (R.pending && R.end - R.beg <= A.short_list) {
-      process_own<OPAQUE, COUNT>(A, R);
-      R.pending = false;
-      if (R.t1 < 0.0f) R.active = false;
-    }
+    process_flat<OPAQUE, COUNT>(A, R);
     // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
     while (pm) {

@@ -20,7 +20,7 @@ constexpr float kCoordMax = 768.0f;
 constexpr float kTStop = 1e-4f;                // transmittance where a ray stops
 constexpr int kMaxRepairRounds = 4;
 constexpr uint32_t kRayQueueLimit = 8;          // culled voxels one ray queues per round
-constexpr uint32_t kShortList = 64;             // trace: lists a lane processes on its own
+constexpr uint32_t kShortList = 512;            // trace: longer lists go to the whole-warp path
 
 // per-vertex flag bits, stored in pos[i].w as raw bits
 constexpr uint32_t kFirst = 1u, kLast = 2u, kClipOn = 4u;
