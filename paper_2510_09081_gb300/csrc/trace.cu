@@ -45,7 +45,7 @@ namespace vrt {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
-constexpr int kOwnKeys = 32;              // transparent, own list: keys kept per scan (shared memory)
+constexpr int kRayKeys = 32;              // transparent, shared entries: hit slots per ray (shared memory)
 constexpr int kTraceThreads = 128;
 constexpr float kConeTan = 1.1180340f;    // tan(half angle), cos(half angle) = 2/3
 constexpr int kConeSteps = 4;             // samples per cone: t = 1, 2.118, 4.486, 9.502 (<= 16)
@@ -466,94 +466,17 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   }
 }
 
-// A lane processes its own pending voxel (short lists): same acceptance and
-// (depth, id) order as the shared path, with the keys in registers.
-template <bool OPAQUE, bool COUNT>
-__device__ void process_own(const TraceArgs& A, Ray& R) {
-  const float r2 = A.g.r * A.g.r;
-  const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
-  unsigned n_cap = 0;
-  if (COUNT) {
-    ++R.n_vox;
-    R.n_entries += R.end - R.beg;
-  }
-  if (OPAQUE) {
-    unsigned long long best = ~0ull;
-    for (uint32_t s = R.beg; s < R.end; ++s) {
-      const unsigned long long k = entry_key<COUNT>(A, s, R.o, R.d, R.vt0, R.vt1, r2, rrm, n_cap);
-      best = k < best ? k : best;
-    }
-    if (COUNT) R.n_cap += n_cap;
-    if (best != ~0ull) {
-      const uint32_t id = (uint32_t)(best & 0xffffffffu);
-      const float t = __uint_as_float((uint32_t)(best >> 32));
-      float3 c = tangent_colour(A, id);
-      if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
-      R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
-      R.T *= (1.0f - A.alpha);
-      R.first_id = (int)id;
-      R.first_t = t;
-      R.active = false;
-    }
-    return;
-  }
-  // this lane's sorted keys: key q at s_key[q * kTraceThreads + threadIdx.x]
-  extern __shared__ unsigned long long s_key[];
-  unsigned long long* kb = s_key + threadIdx.x;
-  const float om = 1.0f - A.alpha;
-  unsigned long long last = 0ull;
-  for (;;) {
-    uint32_t nacc = 0;
-    int nk = 0;
-    for (uint32_t s = R.beg; s < R.end; ++s) {
-      const unsigned long long k = entry_key<COUNT>(A, s, R.o, R.d, R.vt0, R.vt1, r2, rrm, n_cap);
-      if (k == ~0ull || k <= last) continue;
-      ++nacc;
-      if (nk == kOwnKeys && k >= kb[(kOwnKeys - 1) * kTraceThreads]) continue;
-      int q = nk < kOwnKeys ? nk++ : kOwnKeys - 1;
-      while (q > 0 && kb[(q - 1) * kTraceThreads] > k) {
-        kb[q * kTraceThreads] = kb[(q - 1) * kTraceThreads];
-        --q;
-      }
-      kb[q * kTraceThreads] = k;
-    }
-    for (int q = 0; q < nk && R.T >= kTStop; ++q) {
-      const unsigned long long kq = kb[q * kTraceThreads];
-      const uint32_t id = (uint32_t)(kq & 0xffffffffu);
-      const float t = __uint_as_float((uint32_t)(kq >> 32));
-      float3 c = tangent_colour(A, id);
-      if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
-      const float w = R.T * A.alpha;
-      R.C[0] = fmaf(w, c.x, R.C[0]);
-      R.C[1] = fmaf(w, c.y, R.C[1]);
-      R.C[2] = fmaf(w, c.z, R.C[2]);
-      R.T *= om;
-      if (R.first_id < 0) {
-        R.first_id = (int)id;
-        R.first_t = t;
-      }
-      last = kq;
-    }
-    if (R.T < kTStop) {
-      R.active = false;
-      break;
-    }
-    if (nacc <= (uint32_t)kOwnKeys) break;
-  }
-  if (COUNT) R.n_cap += n_cap;
-}
-
 // The pending voxels of the warp's lanes with lists up to A.short_list
 // entries, processed together: their entries are numbered one after another
 // (lane by lane) and the warp takes 32 at a time, one (ray, entry) pair per
 // lane, so lanes with short lists do not wait for the longest one. A hit goes
 // to its ray's slots in shared memory (the nearest key for an opaque ray; up to
-// kOwnKeys keys of a transparent ray, sorted and composited by the ray's own
+// kRayKeys keys of a transparent ray, sorted and composited by the ray's own
 // lane afterwards). A transparent ray with more hits in the voxel keeps its
 // voxel pending for the whole-warp path, which starts it again from scratch.
 template <bool OPAQUE, bool COUNT>
 __device__ void process_flat(const TraceArgs& A, Ray& R) {
-  extern __shared__ unsigned long long s_key[];  // [kOwnKeys][kTraceThreads]
+  extern __shared__ unsigned long long s_key[];  // [kRayKeys][kTraceThreads]
   __shared__ float4 s_ray[2][kTraceThreads];      // (o, t_enter), (d, t_exit)
   __shared__ uint32_t s_cnt[kTraceThreads];
   __shared__ unsigned long long s_best[kTraceThreads];
@@ -597,7 +520,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
           atomicMin(&s_best[wb + j], k);
         } else {
           const uint32_t slot = atomicAdd(&s_cnt[wb + j], 1u);
-          if (slot < (uint32_t)kOwnKeys) s_key[slot * kTraceThreads + wb + j] = k;
+          if (slot < (uint32_t)kRayKeys) s_key[slot * kTraceThreads + wb + j] = k;
         }
       }
     }
@@ -627,7 +550,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     return;
   }
   const uint32_t nk = s_cnt[tid];
-  if (nk > (uint32_t)kOwnKeys) return;  // stays pending: the whole-warp path redoes it
+  if (nk > (uint32_t)kRayKeys) return;  // stays pending: the whole-warp path redoes it
   if (COUNT) {
     ++R.n_vox;
     R.n_entries += len;
@@ -872,7 +795,7 @@ void launch_one(const TraceArgs& a, size_t smem, cudaStream_t s) {
 }
 
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
-  const size_t smem = K == 1 ? 0 : sizeof(unsigned long long) * kOwnKeys * kTraceThreads;
+  const size_t smem = K == 1 ? 0 : sizeof(unsigned long long) * kRayKeys * kTraceThreads;
   if (a.count) {
     if (K == 1) launch_one<true, true>(a, smem, s);
     else launch_one<false, true>(a, smem, s);
