@@ -469,19 +469,23 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
 // The pending voxels of the warp's lanes with lists up to A.short_list
 // entries, processed together: their entries are numbered one after another
 // (lane by lane) and the warp takes 32 at a time, one (ray, entry) pair per
-// lane, so lanes with short lists do not wait for the longest one. A hit goes
-// to its ray's slots in shared memory (the nearest key for an opaque ray; up to
-// kRayKeys keys of a transparent ray, sorted and composited by the ray's own
-// lane afterwards). A transparent ray with more hits in the voxel keeps its
-// voxel pending for the whole-warp path, which starts it again from scratch.
+// lane, so lanes with short lists do not wait for the longest one. Pairs that
+// pass the line-distance test are queued per warp in shared memory and get the
+// capsule test 32 at a time. A hit goes to its ray's slots in shared memory
+// (the nearest key for an opaque ray; up to kRayKeys keys of a transparent
+// ray, sorted and composited by the ray's own lane afterwards). A transparent
+// ray with more hits in the voxel keeps its voxel pending for the whole-warp
+// path, which starts it again from scratch.
 template <bool OPAQUE, bool COUNT>
 __device__ void process_flat(const TraceArgs& A, Ray& R) {
   extern __shared__ unsigned long long s_key[];  // [kRayKeys][kTraceThreads]
   __shared__ float4 s_ray[2][kTraceThreads];      // (o, t_enter), (d, t_exit)
   __shared__ uint32_t s_cnt[kTraceThreads];
   __shared__ unsigned long long s_best[kTraceThreads];
+  __shared__ uint2 s_q[kTraceThreads / 32][64];   // (segment id, owner lane) queued for the capsule test
   const int lane = threadIdx.x & 31;
   const int tid = threadIdx.x, wb = tid & ~31;
+  const unsigned lt = (1u << lane) - 1u;
   const bool take = R.pending && R.end - R.beg <= A.short_list;
   const uint32_t len = take ? R.end - R.beg : 0u;
   uint32_t incl = len;
@@ -503,19 +507,20 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
   const float r2 = A.g.r * A.g.r;
   const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
   unsigned n_cap = 0;
-  for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-    const uint32_t gq = t0 + lane;
-    int j = 0;
-#pragma unroll
-    for (int st = 16; st > 0; st >>= 1)
-      if (__shfl_sync(FULL, incl, j + st - 1) <= gq) j += st;
-    j = min(j, 31);
-    const uint32_t fj = __shfl_sync(FULL, first, j);
-    if (gq < total) {
+  uint2* q = s_q[tid >> 5];
+  uint32_t qn = 0;  // queued pairs (warp-uniform)
+  // capsule test of queued pair `lane` for lanes below cnt
+  auto capsule_stage = [&](uint32_t cnt) {
+    if ((uint32_t)lane < cnt) {
+      const uint2 it = q[lane];
+      const uint32_t id = it.x;
+      const int j = (int)it.y;
+      const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
       const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
-      const unsigned long long k =
-          entry_key<COUNT>(A, fj + gq, f3(ro), f3(rd), ro.w, rd.w, r2, rrm, n_cap);
-      if (k != ~0ull) {
+      if (COUNT) ++n_cap;
+      const float t = capsule_entry(f3(ro), f3(rd), f3(p0), f3(p1), r2);
+      if (t >= ro.w && t < rd.w && clip_keeps(A, f3(ro) + t * f3(rd), p0, p1, id)) {
+        const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | id;
         if (OPAQUE) {
           atomicMin(&s_best[wb + j], k);
         } else {
@@ -524,7 +529,42 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
         }
       }
     }
+  };
+  for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+    const uint32_t gq = t0 + lane;
+    int j = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+      if (__shfl_sync(FULL, incl, j + st - 1) <= gq) j += st;
+    j = min(j, 31);
+    const uint32_t fj = __shfl_sync(FULL, first, j);
+    bool pass = false;
+    uint32_t id = 0;
+    if (gq < total) {
+      id = __ldg(&A.g.lists[fj + gq]);
+      if (id + 1 >= A.n_vert) {
+        set_err(A.g.st, kErrBounds);
+      } else {
+        const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
+        const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
+        pass = lines_may_meet(f3(ro), f3(rd), f3(p0), f3(p1), rrm);
+      }
+    }
+    const unsigned m = __ballot_sync(FULL, pass);
+    if (pass) q[qn + __popc(m & lt)] = make_uint2(id, (uint32_t)j);
+    qn += __popc(m);
+    if (qn >= 32) {
+      __syncwarp();
+      capsule_stage(32);
+      __syncwarp();
+      // the pairs past the first 32 move to the front (reads 32.., writes ..31)
+      if ((uint32_t)lane < qn - 32) q[lane] = q[32 + lane];
+      __syncwarp();
+      qn -= 32;
+    }
   }
+  __syncwarp();
+  capsule_stage(qn);
   __syncwarp();
   if (COUNT) R.n_cap += n_cap;
   if (!take) return;

@@ -322,45 +322,43 @@ __device__ __forceinline__ bool lines_may_meet(float3 o, float3 d, float3 a, flo
   return s * s <= rr_margin * nn;
 }
 
-// First entry of the line o + t d (|d| = 1) into the capsule (a, b, r): the
-// smallest entry over the two end balls and the curved side of the finite
-// cylinder (its flat ends lie inside the balls). +inf when the line misses.
-// The perpendicular offsets are formed explicitly so that the discriminants
-// do not cancel when the origin is far away.
+// First entry of the line o + t d (|d| = 1) into the ball of radius^2 r2
+// centred at o - oc; +inf when the line misses it.
+__device__ __forceinline__ float ball_entry(float3 oc, float3 d, float r2) {
+  const float bq = dot3(oc, d);
+  const float3 w = oc - bq * d;
+  const float disc = r2 - dot3(w, w);
+  return disc >= 0.0f ? -bq - sqrtf(disc) : __int_as_float(0x7f800000);
+}
+
+// First entry of the line o + t d (|d| = 1) into the capsule (a, b, r); +inf
+// when the line misses it. Both end balls lie inside the infinite cylinder
+// around the axis, so the line meets the capsule only if it meets that
+// cylinder, and where it enters the cylinder decides the rest: between the two
+// end planes that entry is the capsule's; before a (after b) the line can
+// reach the rest of the capsule only through the ball at a (at b), whose entry
+// is then the capsule's. The perpendicular offsets are formed explicitly so
+// that the discriminants do not cancel when the origin is far away.
 __device__ __forceinline__ float capsule_entry(float3 o, float3 d, float3 a, float3 b, float r2) {
-  float best = __int_as_float(0x7f800000);
-  const float3 oa = o - a, ob = o - b;
-  {
-    const float bq = dot3(oa, d);
-    const float3 w = oa - bq * d;
-    const float disc = r2 - dot3(w, w);
-    if (disc >= 0.0f) best = fminf(best, -bq - sqrtf(disc));
-  }
-  {
-    const float bq = dot3(ob, d);
-    const float3 w = ob - bq * d;
-    const float disc = r2 - dot3(w, w);
-    if (disc >= 0.0f) best = fminf(best, -bq - sqrtf(disc));
-  }
+  const float3 oa = o - a;
   const float3 ba = b - a;
   const float L2 = dot3(ba, ba);
-  if (L2 > 0.0f) {
-    const float inv = 1.0f / L2;
-    const float3 dp = d - (dot3(d, ba) * inv) * ba;
-    const float3 op = oa - (dot3(oa, ba) * inv) * ba;
-    const float A = dot3(dp, dp);
-    if (A > 0.0f) {
-      const float ts = -dot3(op, dp) / A;
-      const float3 w = op + ts * dp;
-      const float disc = r2 - dot3(w, w);
-      if (disc >= 0.0f) {
-        const float t = ts - sqrtf(disc / A);
-        const float y = dot3(oa + t * d, ba);
-        if (y >= 0.0f && y <= L2) best = fminf(best, t);
-      }
-    }
-  }
-  return best;
+  if (!(L2 > 0.0f)) return ball_entry(oa, d, r2);
+  const float inv = 1.0f / L2;
+  const float3 dp = d - (dot3(d, ba) * inv) * ba;
+  const float3 op = oa - (dot3(oa, ba) * inv) * ba;
+  const float A = dot3(dp, dp);
+  if (!(A > 0.0f))  // along the axis: the nearer ball
+    return fminf(ball_entry(oa, d, r2), ball_entry(o - b, d, r2));
+  const float ts = -dot3(op, dp) / A;
+  const float3 w = op + ts * dp;
+  const float disc = r2 - dot3(w, w);
+  if (disc < 0.0f) return __int_as_float(0x7f800000);
+  const float t = ts - sqrtf(disc / A);
+  const float y = dot3(oa + t * d, ba);
+  if (y < 0.0f) return ball_entry(oa, d, r2);
+  if (y > L2) return ball_entry(o - b, d, r2);
+  return t;
 }
 
 }  // namespace vrt
