@@ -29,7 +29,8 @@ struct vrt_grid_s {
   float4* pos = nullptr;
   float4* nrm = nullptr;
   // voxels
-  uint32_t *word = nullptr, *cur = nullptr, *vis = nullptr, *occb = nullptr;
+  uint32_t *word = nullptr, *cur = nullptr, *vis = nullptr;
+  uint8_t *bdist = nullptr, *btmp = nullptr;  // empty-brick distance field and its scratch
   uint32_t* need = nullptr;
   uint8_t* eroded = nullptr;
   uint32_t* lists = nullptr;
@@ -104,7 +105,7 @@ GridDev gdev(vrt_grid g) {
   d.corr = (g->r / d.r_clamp) * (g->r / d.r_clamp);
   d.occ_scale = (float)g->occ_scale;
   d.force_exact = g->force_exact;
-  d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.occb = g->occb;
+  d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.bdist = g->bdist;
   d.lists = g->lists; d.list_cap = g->list_cap;
   d.xq = g->xq; d.xq_cap = g->xq_cap;
   d.rec = g->rec; d.rec_cap = (uint32_t)g->list_cap;
@@ -223,7 +224,7 @@ void free_all(vrt_grid g) {
     for (int j = 0; j < 2; ++j)
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
   dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
-  dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->occb);
+  dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->bdist); dfree(g->btmp);
   dfree(g->need); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
   dfree(g->xq); dfree(g->rec);
   dfree(g->mips); dfree(g->vq[0]); dfree(g->vq[1]); dfree(g->pq[0]); dfree(g->pq[1]);
@@ -265,7 +266,8 @@ vrt_status vrt_create_grid(const vrt_grid_desc* desc, void* cuda_stream, vrt_gri
   chk(dalloc(&g->cur, nv));
   chk(dalloc(&g->vis, nv / 32));
   chk(dalloc(&g->need, nv / 32));
-  chk(dalloc(&g->occb, (nb + 31) / 32));
+  chk(dalloc(&g->bdist, nb));
+  chk(dalloc(&g->btmp, nb));
   g->n_tiles = (uint32_t)(nv / 4096);
   chk(dalloc(&g->tile_state, g->n_tiles));
   chk(dalloc(&g->st, 1));
@@ -413,6 +415,7 @@ vrt_status vrt_voxelize(vrt_grid g) {
   stage_mark(g, ST_INGEST, 1);
   stage_mark(g, ST_PASS1, 0);
   g->launches += launch_pass1(g->pos, g->nrm, g->V, gdev(g), g->stream);
+  g->launches += launch_brick_dist(gdev(g), g->btmp, g->bdist, g->stream);
   stage_mark(g, ST_PASS1, 1);
   VRT_CUDA(g, cudaGetLastError());
   g->stage = 2;

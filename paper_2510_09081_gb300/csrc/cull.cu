@@ -12,7 +12,8 @@
 // occupancy estimate's excess over the true tube volume (about 4/3 for thin
 // tubes under the PWAA clamp). A voxel is marked visible unless
 // the depth in front of it exceeds ln(1e4) + 3, past the depth where a ray
-// stops. The marks decide which voxels get lists; voxels a ray later needs but
+// stops. The march crosses cubes of empty bricks in one step, using the
+// distance field built after pass 1. The marks decide which voxels get lists; voxels a ray later needs but
 // that were left unmarked are listed by the trace's repair rounds, so the
 // marks only affect speed.
 #include <cmath>
@@ -90,46 +91,66 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
       tmax = dist;
     }
     if (inside) {
-      // march voxel by voxel from the centre toward the camera
+      // march from the centre toward the camera, voxel by voxel through
+      // bricks with occupied voxels and across cubes of empty bricks (which
+      // add no depth) in one step
       const int n = g.n;
-      int p[3] = {x, y, z};
-      int step[3];
-      float inv[3], og[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float dk = cmp3(dir, k);
-        og[k] = cmp3(c, k);
-        step[k] = dk > 0.0f ? 1 : (dk < 0.0f ? -1 : 0);
-        inv[k] = dk != 0.0f ? 1.0f / dk : 0.0f;
-      }
-      float depth = 0.0f, tprev = 0.0f;
+      int px = x, py = y, pz = z;
+      const int sx = dir.x > 0.0f ? 1 : (dir.x < 0.0f ? -1 : 0);
+      const int sy = dir.y > 0.0f ? 1 : (dir.y < 0.0f ? -1 : 0);
+      const int sz = dir.z > 0.0f ? 1 : (dir.z < 0.0f ? -1 : 0);
+      const float ix = dir.x != 0.0f ? 1.0f / dir.x : 0.0f;
+      const float iy = dir.y != 0.0f ? 1.0f / dir.y : 0.0f;
+      const float iz = dir.z != 0.0f ? 1.0f / dir.z : 0.0f;
+      // parameter where the march leaves [lo, hi] along one axis
+      auto leave = [](int s, int lo, int hi, float o, float inv) {
+        return s != 0 ? ((float)(s > 0 ? hi : lo) - o) * inv : __int_as_float(0x7f800000);
+      };
+      float depth = 0.0f, tcur = 0.0f;
+      bool counted = false;  // the voxel itself adds nothing to the depth in front of it
       visible = true;
-      for (int it = 0; it < 3 * n; ++it) {
-        float te = __int_as_float(0x7f800000);
-        int ke = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if (step[k] == 0) continue;
-          const float tk = ((float)(step[k] > 0 ? p[k] + 1 : p[k]) - og[k]) * inv[k];
-          if (tk < te) { te = tk; ke = k; }
+      for (int it = 0; it < 3 * n + 16; ++it) {
+        const float tx = leave(sx, px, px + 1, c.x, ix);
+        const float ty = leave(sy, py, py + 1, c.y, iy);
+        const float tz = leave(sz, pz, pz + 1, c.z, iz);
+        const float te = fminf(tx, fminf(ty, tz));
+        if (counted) {
+          const float e = (float)__ldg(&eroded[brick_index(px, py, pz, g.log2nb)]) * (1.0f / 255.0f);
+          depth = fmaf(cc.kappa * e, fminf(te, tmax) - tcur, depth);
+          if (depth > kCullDepth) { visible = false; break; }
         }
+        counted = true;
         if (te >= tmax) break;
-        p[ke] += step[ke];
-        if (p[ke] < 0 || p[ke] >= n) break;
-        float tn = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if (step[k] == 0) continue;
-          tn = fminf(tn, ((float)(step[k] > 0 ? p[k] + 1 : p[k]) - og[k]) * inv[k]);
+        if (te == tx) px += sx; else if (te == ty) py += sy; else pz += sz;
+        if ((unsigned)px >= (unsigned)n || (unsigned)py >= (unsigned)n || (unsigned)pz >= (unsigned)n) break;
+        tcur = te;
+        bool done = false;
+        for (int sk = 0; sk < 3 * n; ++sk) {
+          const uint32_t bidx = ((uint32_t)(pz >> 2) << (2 * g.log2nb)) |
+                                ((uint32_t)(py >> 2) << g.log2nb) | (uint32_t)(px >> 2);
+          const int kd = __ldg(&g.bdist[bidx]);
+          if (kd == 0) break;
+          const int ext = 4 * (kd - 1), w = 4 + 2 * ext;
+          const int bx = (px & ~3) - ext, by = (py & ~3) - ext, bz = (pz & ~3) - ext;
+          const float ux = leave(sx, bx, bx + w, c.x, ix);
+          const float uy = leave(sy, by, by + w, c.y, iy);
+          const float uz = leave(sz, bz, bz + w, c.z, iz);
+          const float tb = fminf(ux, fminf(uy, uz));
+          if (tb >= tmax) { done = true; break; }
+          const int qx = min(min(bx + w, n) - 1, max(max(bx, 0), (int)floorf(fmaf(tb, dir.x, c.x))));
+          const int qy = min(min(by + w, n) - 1, max(max(by, 0), (int)floorf(fmaf(tb, dir.y, c.y))));
+          const int qz = min(min(bz + w, n) - 1, max(max(bz, 0), (int)floorf(fmaf(tb, dir.z, c.z))));
+          if (tb == ux) { px = sx > 0 ? bx + w : bx - 1; py = qy; pz = qz; }
+          else if (tb == uy) { py = sy > 0 ? by + w : by - 1; px = qx; pz = qz; }
+          else { pz = sz > 0 ? bz + w : bz - 1; px = qx; py = qy; }
+          if ((unsigned)px >= (unsigned)n || (unsigned)py >= (unsigned)n || (unsigned)pz >= (unsigned)n) {
+            done = true;
+            break;
+          }
+          tcur = tb;
         }
-        tn = fminf(tn, tmax);
-        const float e = (float)__ldg(&eroded[brick_index(p[0], p[1], p[2], g.log2nb)]) *
-                        (1.0f / 255.0f);
-        depth = fmaf(cc.kappa * e, tn - te, depth);
-        tprev = te;
-        if (depth > kCullDepth) { visible = false; break; }
+        if (done) break;
       }
-      (void)tprev;
     }
   }
   const uint32_t m = __ballot_sync(0xffffffffu, visible);

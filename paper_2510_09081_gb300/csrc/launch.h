@@ -53,6 +53,8 @@ int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* p
                    DevStatus* st, cudaStream_t s);
 int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,
                   cudaStream_t s);
+// Empty-brick distance field from the counts of pass 1 (tmp: one byte per brick).
+int launch_brick_dist(const GridDev& g, uint8_t* tmp, uint8_t* dist, cudaStream_t s);
 // Pass 2 over the fragment records. mode 0: every occupied voxel has a list;
 // 1: voxels marked by the cull; 2: repair, only voxels whose `need` bit is set
 // (skipped when *pending is 0).

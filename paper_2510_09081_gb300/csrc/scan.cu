@@ -30,12 +30,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_prefix;
-  __shared__ uint32_t s_occb[2];
   __shared__ unsigned long long s_red[4][kScanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     s_tile = atomicAdd(&g.st->scan_tile_counter, 1u);
-    s_occb[0] = s_occb[1] = 0;
   }
   __syncthreads();
   const uint32_t tile = s_tile;
@@ -62,16 +60,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
     val[k] = ((visw >> k) & 1u) ? c : 0u;
     visible += val[k] != 0;
     sum += val[k];
-  }
-  // bricks with an occupied voxel: 4 threads per brick
-  {
-    uint32_t any = occupied != 0;
-    any |= __shfl_xor_sync(0xffffffffu, any, 1);
-    any |= __shfl_xor_sync(0xffffffffu, any, 2);
-    if ((lane & 3) == 0 && any) {
-      const uint32_t b = (uint32_t)(tid >> 2);  // brick within the tile, 0..63
-      atomicOr(&s_occb[b >> 5], 1u << (b & 31));
-    }
   }
   // block exclusive scan of per-thread sums
   uint32_t incl = sum;
@@ -148,7 +136,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
 #pragma unroll
   for (int q = 0; q < kScanItems / 4; ++q)
     dst[q] = make_uint4(outv[4 * q], outv[4 * q + 1], outv[4 * q + 2], outv[4 * q + 3]);
-  if (tid < 2) g.occb[tile * 2 + tid] = s_occb[tid];
 
   // counters
   unsigned long long r0 = cf, r1 = of, r2 = ((unsigned long long)visible << 32) | occupied;

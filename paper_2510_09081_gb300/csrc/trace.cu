@@ -2,8 +2,9 @@
 //
 // One ray per pixel; a warp owns an 8x4 pixel tile (in the repair re-trace, 32
 // queued pixels). Each lane steps its own ray by 3D-DDA (Amanatides & Woo)
-// through the grid box, crossing bricks with no occupied voxel in one step
-// (empty-space skipping), until it reaches a voxel with a list. The warp then
+// through the grid box until it reaches a voxel with a list; in a brick with
+// no occupied voxel it crosses, in one step, the whole cube of empty bricks
+// that the distance field built after pass 1 guarantees around it. The warp then
 // numbers the entries of all its lanes' pending lists one after another and
 // takes them 32 at a time, one (ray, entry) pair per lane, so no lane idles on
 // another lane's longer list. Very long lists, and a transparent ray with more
@@ -214,25 +215,28 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
     if (COUNT) ++R.n_steps;
     const uint32_t bidx = ((uint32_t)(R.vz >> 2) << (2 * A.g.log2nb)) |
                           ((uint32_t)(R.vy >> 2) << A.g.log2nb) | (uint32_t)(R.vx >> 2);
-    if (!bit_at(A.g.occb, bidx)) {
-      // cross the whole empty brick
-      const int bx = R.vx & ~3, by = R.vy & ~3, bz = R.vz & ~3;
-      const float tx = exit_t(R.sx, bx, bx + 4, R.ooi.x, R.inv.x);
-      const float ty = exit_t(R.sy, by, by + 4, R.ooi.y, R.inv.y);
-      const float tz = exit_t(R.sz, bz, bz + 4, R.ooi.z, R.inv.z);
+    const int kd = __ldg(&A.g.bdist[bidx]);
+    if (kd > 0) {
+      // cross the cube of empty bricks within kd - 1 of this one: low corner
+      // (bx, by, bz), side w voxels
+      const int ext = 4 * (kd - 1), w = 4 + 2 * ext;
+      const int bx = (R.vx & ~3) - ext, by = (R.vy & ~3) - ext, bz = (R.vz & ~3) - ext;
+      const float tx = exit_t(R.sx, bx, bx + w, R.ooi.x, R.inv.x);
+      const float ty = exit_t(R.sy, by, by + w, R.ooi.y, R.inv.y);
+      const float tz = exit_t(R.sz, bz, bz + w, R.ooi.z, R.inv.z);
       const float tb = fminf(tx, fminf(ty, tz));
       if (tb > R.t1) return false;
-      const int cx = min(bx + 3, max(bx, (int)floorf(fmaf(tb, R.d.x, R.o.x))));
-      const int cy = min(by + 3, max(by, (int)floorf(fmaf(tb, R.d.y, R.o.y))));
-      const int cz = min(bz + 3, max(bz, (int)floorf(fmaf(tb, R.d.z, R.o.z))));
+      const int cx = min(min(bx + w, n) - 1, max(max(bx, 0), (int)floorf(fmaf(tb, R.d.x, R.o.x))));
+      const int cy = min(min(by + w, n) - 1, max(max(by, 0), (int)floorf(fmaf(tb, R.d.y, R.o.y))));
+      const int cz = min(min(bz + w, n) - 1, max(max(bz, 0), (int)floorf(fmaf(tb, R.d.z, R.o.z))));
       if (tb == tx) {
-        R.vx = R.sx > 0 ? bx + 4 : bx - 1; R.vy = cy; R.vz = cz;
+        R.vx = R.sx > 0 ? bx + w : bx - 1; R.vy = cy; R.vz = cz;
         if (R.vx < 0 || R.vx >= n) return false;
       } else if (tb == ty) {
-        R.vy = R.sy > 0 ? by + 4 : by - 1; R.vx = cx; R.vz = cz;
+        R.vy = R.sy > 0 ? by + w : by - 1; R.vx = cx; R.vz = cz;
         if (R.vy < 0 || R.vy >= n) return false;
       } else {
-        R.vz = R.sz > 0 ? bz + 4 : bz - 1; R.vx = cx; R.vy = cy;
+        R.vz = R.sz > 0 ? bz + w : bz - 1; R.vx = cx; R.vy = cy;
         if (R.vz < 0 || R.vz >= n) return false;
       }
       R.tcur = fmaxf(R.tcur, tb);

@@ -21,6 +21,7 @@ constexpr float kTStop = 1e-4f;                // transmittance where a ray stop
 constexpr int kMaxRepairRounds = 4;
 constexpr uint32_t kRayQueueLimit = 8;          // culled voxels one ray queues per round
 constexpr uint32_t kShortList = 512;            // trace: longer lists go to the whole-warp path
+constexpr int kBrickDistMax = 15;               // cap of the empty-brick distance field
 
 // per-vertex flag bits, stored in pos[i].w as raw bits
 constexpr uint32_t kFirst = 1u, kLast = 2u, kClipOn = 4u;
@@ -86,7 +87,7 @@ struct GridDev {
   uint32_t* word;          // [n^3] packed (occupancy code sum << 16) | count
   uint32_t* cur;           // [n^3] list end cursor (start = cur - count)
   uint32_t* vis;           // [n^3 / 32] voxel has a list
-  uint32_t* occb;          // [bricks / 32] brick has an occupied voxel
+  const uint8_t* bdist;    // [bricks] Chebyshev distance (bricks) to an occupied brick, capped
   uint32_t* lists;         // [list_cap]
   unsigned long long list_cap;
   uint2* xq;               // [xq_cap] undecided (segment id, packed voxel) pairs
