@@ -11,10 +11,11 @@
 // same width bound (the slab's extent along a minor axis is at most
 // |d_ai / d_a0| + 2 * half-extent), so candidate q of a segment decodes in O(1).
 //
-// Work layout: each lane loads one segment (coalesced) and sets up its walk;
-// the warp numbers the candidates of its 32 segments consecutively and takes
-// them 32 at a time, each lane pulling its segment's walk by shuffles, so
-// segments of different lengths do not leave lanes idle. The fp32 filter decides almost every candidate; pairs it
+// Work layout: each lane loads one segment (coalesced), sets up its walk and
+// stores it, packed, in shared memory; the warp numbers the candidates of its
+// 32 segments consecutively and takes them 32 at a time, each lane reading the
+// walk of the segment its candidate belongs to, so segments of different
+// lengths do not leave lanes idle. The fp32 filter decides almost every candidate; pairs it
 // cannot decide go to a queue that a separate kernel decides exactly (keeping
 // the 128-bit integer path out of the hot kernels' registers).
 //
@@ -39,16 +40,18 @@ struct Walk {
   uint32_t n;  // candidates: slabs * W1 * W2
 };
 
-// Minor-axis voxel ranges of slab c (clamped to the grid).
-__device__ __forceinline__ void slab_box(const Walk& w, int n, int c, int& j0, int& j1, int& l0,
-                                         int& l1) {
-  const float x0 = fmaxf((float)c, w.lo_m), x1 = fminf((float)(c + 1), w.hi_m);
-  const float p1a = fmaf(x0 - w.am, w.s1, w.a1), p1b = fmaf(x1 - w.am, w.s1, w.a1);
-  const float p2a = fmaf(x0 - w.am, w.s2, w.a2), p2b = fmaf(x1 - w.am, w.s2, w.a2);
-  j0 = max(0, (int)floorf(fminf(p1a, p1b) - w.rho1));
-  j1 = min(n - 1, (int)floorf(fmaxf(p1a, p1b) + w.rho1));
-  l0 = max(0, (int)floorf(fminf(p2a, p2b) - w.rho2));
-  l1 = min(n - 1, (int)floorf(fmaxf(p2a, p2b) + w.rho2));
+// Minor-axis voxel ranges of slab c (clamped to the grid): the axis line
+// a_k + (x - a_m) s_k over the slab's part of [lo_m, hi_m], widened by rho_k.
+__device__ __forceinline__ void slab_box(float am, float a1, float a2, float s1, float s2,
+                                         float rho1, float rho2, float lo_m, float hi_m, int n,
+                                         int c, int& j0, int& j1, int& l0, int& l1) {
+  const float x0 = fmaxf((float)c, lo_m), x1 = fminf((float)(c + 1), hi_m);
+  const float p1a = fmaf(x0 - am, s1, a1), p1b = fmaf(x1 - am, s1, a1);
+  const float p2a = fmaf(x0 - am, s2, a2), p2b = fmaf(x1 - am, s2, a2);
+  j0 = max(0, (int)floorf(fminf(p1a, p1b) - rho1));
+  j1 = min(n - 1, (int)floorf(fmaxf(p1a, p1b) + rho1));
+  l0 = max(0, (int)floorf(fminf(p2a, p2b) - rho2));
+  l1 = min(n - 1, (int)floorf(fmaxf(p2a, p2b) + rho2));
 }
 
 __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g, Walk& w) {
@@ -77,7 +80,7 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
   int W1 = 1, W2 = 1;
   for (int c = w.c0; c <= c1; ++c) {
     int j0, j1, l0, l1;
-    slab_box(w, n, c, j0, j1, l0, l1);
+    slab_box(w.am, w.a1, w.a2, w.s1, w.s2, w.rho1, w.rho2, w.lo_m, w.hi_m, n, c, j0, j1, l0, l1);
     W1 = max(W1, j1 - j0 + 1);
     W2 = max(W2, l1 - l0 + 1);
   }
@@ -88,47 +91,46 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
   w.inv_w2 = 1.0f / (float)w.W2;
 }
 
-__device__ __forceinline__ Walk shfl_walk(const Walk& w, int src) {
-  Walk r;
-  r.a = make_float3(__shfl_sync(FULLW, w.a.x, src), __shfl_sync(FULLW, w.a.y, src),
-                    __shfl_sync(FULLW, w.a.z, src));
-  r.b = make_float3(__shfl_sync(FULLW, w.b.x, src), __shfl_sync(FULLW, w.b.y, src),
-                    __shfl_sync(FULLW, w.b.z, src));
-  r.am = __shfl_sync(FULLW, w.am, src);
-  r.a1 = __shfl_sync(FULLW, w.a1, src);
-  r.a2 = __shfl_sync(FULLW, w.a2, src);
-  r.s1 = __shfl_sync(FULLW, w.s1, src);
-  r.s2 = __shfl_sync(FULLW, w.s2, src);
-  r.rho1 = __shfl_sync(FULLW, w.rho1, src);
-  r.rho2 = __shfl_sync(FULLW, w.rho2, src);
-  r.lo_m = __shfl_sync(FULLW, w.lo_m, src);
-  r.hi_m = __shfl_sync(FULLW, w.hi_m, src);
-  r.inv_w12 = __shfl_sync(FULLW, w.inv_w12, src);
-  r.inv_w2 = __shfl_sync(FULLW, w.inv_w2, src);
-  r.m = __shfl_sync(FULLW, w.m, src);
-  r.c0 = __shfl_sync(FULLW, w.c0, src);
-  r.W1 = __shfl_sync(FULLW, w.W1, src);
-  r.W2 = __shfl_sync(FULLW, w.W2, src);
-  r.n = __shfl_sync(FULLW, w.n, src);
-  return r;
+// A walk as four float4s in shared memory (plus the clip normals in two more):
+//   w0 = (a, s1), w1 = (b, s2), w2 = (rho1, rho2, lo_m, hi_m),
+//   w3 = (1 / (W1 W2), 1 / W2, bits, first candidate number of the warp),
+//   bits = m | c0 << 2 | W1 << 11 | W2 << 19 | clip flags << 27.
+// W1, W2 <= 2 + |s_k| + 2 rho_k < 16 since radius <= 4, and c0 < 512.
+struct PackedWalk {
+  float4 w0, w1, w2, w3;
+};
+
+__device__ __forceinline__ PackedWalk pack_walk(const Walk& w, uint32_t clip, uint32_t first) {
+  PackedWalk p;
+  p.w0 = make_float4(w.a.x, w.a.y, w.a.z, w.s1);
+  p.w1 = make_float4(w.b.x, w.b.y, w.b.z, w.s2);
+  p.w2 = make_float4(w.rho1, w.rho2, w.lo_m, w.hi_m);
+  const uint32_t bits = (uint32_t)w.m | ((uint32_t)w.c0 << 2) | ((uint32_t)w.W1 << 11) |
+                        ((uint32_t)w.W2 << 19) | (clip << 27);
+  p.w3 = make_float4(w.inv_w12, w.inv_w2, __uint_as_float(bits), __uint_as_float(first));
+  return p;
 }
 
-// Candidate q of walk w: its voxel, or false when q falls outside its slab's box.
-__device__ __forceinline__ bool walk_decode(const Walk& w, int n, uint32_t q, int& x, int& y,
-                                            int& z) {
+// Candidate q of a packed walk: its voxel, or false when q falls outside its
+// slab's box.
+__device__ __forceinline__ bool decode_candidate(const PackedWalk& p, int n, uint32_t q, int& x,
+                                                 int& y, int& z) {
+  const uint32_t bits = __float_as_uint(p.w3.z);
+  const int m = bits & 3, c0 = (bits >> 2) & 511, W1 = (bits >> 11) & 255, W2 = (bits >> 19) & 255;
   // (q + 1/2) / w is at least 1/(2w) from an integer, far beyond fp32 error for
   // these small counts, so truncation gives the exact quotient
-  const int w12 = w.W1 * w.W2;
-  const int slab = (int)(((float)q + 0.5f) * w.inv_w12);
-  const int rem = (int)q - slab * w12;
-  const int dj = (int)(((float)rem + 0.5f) * w.inv_w2);
-  const int dl = rem - dj * w.W2;
-  const int c = w.c0 + slab;
+  const int slab = (int)(((float)q + 0.5f) * p.w3.x);
+  const int rem = (int)q - slab * (W1 * W2);
+  const int dj = (int)(((float)rem + 0.5f) * p.w3.y);
+  const int dl = rem - dj * W2;
+  const int c = c0 + slab;
+  const float am = m == 0 ? p.w0.x : (m == 1 ? p.w0.y : p.w0.z);
+  const float a1 = m == 0 ? p.w0.y : p.w0.x;
+  const float a2 = m == 2 ? p.w0.y : p.w0.z;
   int j0, j1, l0, l1;
-  slab_box(w, n, c, j0, j1, l0, l1);
+  slab_box(am, a1, a2, p.w0.w, p.w1.w, p.w2.x, p.w2.y, p.w2.z, p.w2.w, n, c, j0, j1, l0, l1);
   const int j = j0 + dj, l = l0 + dl;
   if (j > j1 || l > l1) return false;
-  const int m = w.m;
   x = m == 0 ? c : j;
   y = m == 1 ? c : (m == 0 ? j : l);
   z = m == 2 ? c : l;
@@ -215,7 +217,11 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   unsigned long long F = 0, sq = 0, ex = 0;
   const unsigned lt = (1u << lane) - 1u;
   __shared__ unsigned long long s_rec[8][kWarpRecords];
+  // every lane's walk, packed, read by the lanes that take its candidates
+  __shared__ PackedWalk s_w[256];
+  __shared__ float4 s_n[2][256];  // clip normals at v0 and v1
   unsigned long long* srec = s_rec[threadIdx.x >> 5];
+  const int tid = threadIdx.x, wb = tid & ~31;
   int wcount = 0;  // records staged by this warp (uniform)
   // The warp's candidates, segment after segment, are numbered 0..total-1;
   // lane l takes number t0 + l and finds its segment by a binary search over
@@ -227,6 +233,12 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     if (lane >= o) incl += v;
   }
   const uint32_t total = __shfl_sync(FULLW, incl, 31);
+  if (w.n) {
+    s_w[tid] = pack_walk(w, en, incl - w.n);
+    s_n[0][tid] = make_float4(n0.x, n0.y, n0.z, 0.0f);
+    s_n[1][tid] = make_float4(n1.x, n1.y, n1.z, 0.0f);
+  }
+  __syncwarp();
   for (uint32_t t0 = 0; t0 < total; t0 += 32) {
     const uint32_t gq = t0 + lane;
     int j = 0;
@@ -234,17 +246,14 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     for (int st = 16; st > 0; st >>= 1)
       if (__shfl_sync(FULLW, incl, j + st - 1) <= gq) j += st;
     j = min(j, 31);
-    const Walk wj = shfl_walk(w, j);
-    const float3 n0j = make_float3(__shfl_sync(FULLW, n0.x, j), __shfl_sync(FULLW, n0.y, j),
-                                   __shfl_sync(FULLW, n0.z, j));
-    const float3 n1j = make_float3(__shfl_sync(FULLW, n1.x, j), __shfl_sync(FULLW, n1.y, j),
-                                   __shfl_sync(FULLW, n1.z, j));
-    const uint32_t enj = __shfl_sync(FULLW, en, j);
-    const uint32_t q = gq - (__shfl_sync(FULLW, incl, j) - wj.n);
     const uint32_t seg = (uint32_t)(base + j);
     int x = 0, y = 0, z = 0, dec = 0;
-    if (gq < total && walk_decode(wj, g.n, q, x, y, z))
-      dec = g.force_exact ? -1 : seg_filter_at(wj.a, wj.b, x, y, z, g.rl);
+    PackedWalk p;
+    if (gq < total) {
+      p = s_w[wb + j];
+      if (decode_candidate(p, g.n, gq - __float_as_uint(p.w3.w), x, y, z))
+        dec = g.force_exact ? -1 : seg_filter_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
+    }
     if (dec < 0) {
       queue_exact(g, seg, x, y, z);
       ++ex;
@@ -252,7 +261,9 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     uint32_t idx = 0;
     if (dec > 0) {
       idx = brick_index(x, y, z, g.log2nb);
-      add_fragment(g, wj.a, wj.b, n0j, n1j, enj & 1u, enj & 2u, x, y, z, F, sq);
+      const uint32_t clip = __float_as_uint(p.w3.z) >> 27;
+      add_fragment(g, f3(p.w0), f3(p.w1), f3(s_n[0][wb + j]), f3(s_n[1][wb + j]), clip & 1u,
+                   clip & 2u, x, y, z, F, sq);
     }
     // stage the warp's records in shared memory; one global append per batch
     const unsigned am = __ballot_sync(FULLW, dec > 0);

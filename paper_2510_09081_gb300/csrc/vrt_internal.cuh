@@ -112,15 +112,19 @@ __device__ __forceinline__ float cmp3(float3 a, int k) { return k == 0 ? a.x : (
 // voxel units relative to the box's lower corner (exact fp32 multiples of
 // 2^-14). Returns 1 (within), 0 (not within) or -1 (too close to call in fp32).
 //
-// Stage 1 takes the point p of the segment nearest the box centre c, w = p - c:
-//   dist(p, box) <= rl                       -> within (p is on the segment)
-//   |w| - (|w_x| + |w_y| + |w_z|) / (2 |w|)  > rl -> not within: the plane
-//     through p with normal w / |w| has the whole segment on one side (p is
-//     the nearest point of a convex set) and the box, whose support along that
-//     normal is half the 1-norm, on the other.
+// Stage 1 takes a point p = a + t d of the segment near the box centre c (t
+// from the projection of c, clamped to [0, 1]), e = c - p:
+//   dist(p, box) <= rl -> within (p is on the segment)
+//   |e| - (|e_x| + |e_y| + |e_z|) / (2 |e|) - reach > rl -> not within: along
+//     the unit normal e / |e| the box lies at least |e| - (half its 1-norm)
+//     beyond p, and the segment reaches at most
+//     reach = max(0, -t d.e, (1 - t) d.e) / |e| beyond p (its endpoints are
+//     p - t d and p + (1 - t) d). This holds for any t, so the projection
+//     needs no exact division.
 // Stage 2 runs Newton steps on the convex, C^1, piecewise-quadratic squared
 // box distance f(t) and brackets its minimum: f(t) is an upper bound, and
-// convexity gives f(t) - |f'(t)| * (t or 1 - t) as a lower bound.
+// convexity gives f(t) - |f'(t)| * (t or 1 - t) as a lower bound, again for
+// any t.
 // Both stages add a rounding allowance proportional to the squared magnitude
 // of the local coordinates.
 __device__ __forceinline__ int seg_box_filter(float3 a, float3 d, float rl) {
@@ -129,7 +133,7 @@ __device__ __forceinline__ int seg_box_filter(float3 a, float3 d, float rl) {
   const float tol = 4.8e-7f * (M + 2.0f) * (M + 2.0f);
   const float dd = dot3(d, d);
   const float3 w = make_float3(0.5f - a.x, 0.5f - a.y, 0.5f - a.z);
-  float t = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, dot3(w, d) / dd)) : 0.0f;
+  float t = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, __fdividef(dot3(w, d), dd))) : 0.0f;
   {
     const float3 e = w - t * d;  // c - p
     const float ex = fmaxf(fabsf(e.x) - 0.5f, 0.0f), ey = fmaxf(fabsf(e.y) - 0.5f, 0.0f),
@@ -139,7 +143,9 @@ __device__ __forceinline__ int seg_box_filter(float3 a, float3 d, float rl) {
     const float e2 = dot3(e, e);
     if (e2 > 0.0f) {
       const float len = sqrtf(e2);
-      const float lb = len - 0.5f * (fabsf(e.x) + fabsf(e.y) + fabsf(e.z)) / len;
+      const float de = dot3(d, e);
+      const float reach = fmaxf(0.0f, fmaxf(-t * de, (1.0f - t) * de));
+      const float lb = len - __fdividef(0.5f * (fabsf(e.x) + fabsf(e.y) + fabsf(e.z)) + reach, len);
       if (lb > rl && lb * lb - tol > rl * rl) return 0;
     }
   }
@@ -159,7 +165,7 @@ __device__ __forceinline__ int seg_box_filter(float3 a, float3 d, float rl) {
     f = ff;
     g = gg;
     if (it == 3 || gp == 0.0f) break;
-    t = fminf(1.0f, fmaxf(0.0f, t - gg / gp));
+    t = fminf(1.0f, fmaxf(0.0f, t - __fdividef(gg, gp)));
   }
   const float rl2 = rl * rl;
   if (f + tol <= rl2) return 1;
@@ -301,7 +307,7 @@ __device__ __forceinline__ float capsule_occupancy(float3 p, float3 a, float3 b,
   const float3 d = b - a;
   const float3 pa = p - a, pb = p - b;
   const float dd = dot3(d, d);
-  const float h = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, dot3(pa, d) / dd)) : 0.0f;
+  const float h = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, __fdividef(dot3(pa, d), dd))) : 0.0f;
   const float3 q = pa - h * d;
   float s = sqrtf(dot3(q, q)) - r_clamp;
   if (en0) s = fmaxf(s, -dot3(pa, n0));
