@@ -47,6 +47,7 @@ struct vrt_grid_s {
   uint32_t vq_cap = 0;
   uint32_t* pq[2] = {nullptr, nullptr};
   uint32_t pq_cap = 0;
+  float4* resume = nullptr;  // [2 * pq_cap] ray state at the first culled voxel
   DevStatus* st = nullptr;
   int force_exact = 0;
   int trace_counters = 0;
@@ -228,6 +229,7 @@ void free_all(vrt_grid g) {
   dfree(g->need); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
   dfree(g->xq); dfree(g->rec);
   dfree(g->mips); dfree(g->vq[0]); dfree(g->vq[1]); dfree(g->pq[0]); dfree(g->pq[1]);
+  dfree(g->resume);
   dfree(g->st);
 }
 
@@ -493,10 +495,11 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   const uint32_t npx = (uint32_t)cam->width * (uint32_t)cam->height;
   if (g->culled && npx > g->pq_cap) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-    dfree(g->pq[0]); dfree(g->pq[1]);
+    dfree(g->pq[0]); dfree(g->pq[1]); dfree(g->resume);
     g->pq_cap = 0;
     VRT_CUDA(g, dalloc(&g->pq[0], npx));
     VRT_CUDA(g, dalloc(&g->pq[1], npx));
+    VRT_CUDA(g, dalloc(&g->resume, 2 * (size_t)npx));
     g->pq_cap = npx;
   }
   TraceArgs a;
@@ -518,6 +521,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.pq_cap = g->pq_cap;
   a.vq = g->vq[0]; a.vq_cnt = &g->st->vq_cnt[0];
   a.pq = g->pq[0]; a.pq_cnt = &g->st->pq_cnt[0];
+  a.resume = g->culled ? g->resume : nullptr;
   // Traces before the next-to-last repair round stop after a few queued
   // voxels (cheap, may need another round); the re-trace of the next-to-last
   // round queues without limit, so the last round always completes.

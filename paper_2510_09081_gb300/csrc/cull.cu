@@ -24,14 +24,6 @@ namespace vrt {
 
 constexpr float kCullDepth = 9.2103404f + 3.0f;  // ln(1e4) + 3
 
-__device__ __forceinline__ void brick_coords(uint32_t idx, int log2nb, int& x, int& y, int& z) {
-  const uint32_t b = idx >> 6, l = idx & 63u;
-  const uint32_t mask = (1u << log2nb) - 1u;
-  x = (int)(((b & mask) << 2) | (l & 3u));
-  y = (int)((((b >> log2nb) & mask) << 2) | ((l >> 2) & 3u));
-  z = (int)(((b >> (2 * log2nb)) << 2) | (l >> 4));
-}
-
 __device__ __forceinline__ uint32_t occ8(const GridDev& g, int x, int y, int z) {
   if ((unsigned)x >= (unsigned)g.n || (unsigned)y >= (unsigned)g.n || (unsigned)z >= (unsigned)g.n)
     return 0u;

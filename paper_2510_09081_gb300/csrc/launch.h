@@ -45,6 +45,8 @@ struct TraceArgs {
   uint32_t vq_cap, pq_cap;
   uint32_t max_queue;        // culled voxels one ray may queue before it stops
   uint32_t* work_next;       // next work item (persistent warps)
+  float4* resume;            // [2 * pixels] state of a ray at its first culled voxel:
+                             // (C, T), (first id bits, first t, voxel index bits, entry t)
   uint32_t short_list;       // lists up to this length share the warp entry by entry
   int count;                 // accumulate trace work counters
 };

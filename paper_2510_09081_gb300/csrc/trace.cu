@@ -264,7 +264,13 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
     }
     if (cnt) {
       if (!bit_at(A.g.vis, idx)) {
-        // culled voxel on the ray: queue it, march on as if it were empty
+        // culled voxel on the ray: queue it, march on as if it were empty; at
+        // the first one, keep the ray's state for the re-trace to resume from
+        if (R.n_queued == 0 && A.resume) {
+          A.resume[2 * R.pix] = make_float4(R.C[0], R.C[1], R.C[2], R.T);
+          A.resume[2 * R.pix + 1] = make_float4(__int_as_float(R.first_id), R.first_t,
+                                                __uint_as_float(idx), tin);
+        }
         const uint32_t bm = 1u << (idx & 31);
         const uint32_t old = atomicOr(&A.need[idx >> 5], bm);
         if (!(old & bm)) {
@@ -341,6 +347,23 @@ __device__ void init_ray(const TraceArgs& A, Ray& R, int px, int py, bool valid)
   R.vx = min(n - 1, max(0, (int)floorf(fmaf(t0, R.d.x, R.o.x))));
   R.vy = min(n - 1, max(0, (int)floorf(fmaf(t0, R.d.y, R.o.y))));
   R.vz = min(n - 1, max(0, (int)floorf(fmaf(t0, R.d.z, R.o.z))));
+}
+
+// A re-traced ray continues from the state it had when it first met a culled
+// voxel (now listed): same colour, transmittance and first hit, at that voxel
+// and its entry parameter, so the result equals a trace from the start.
+__device__ void resume_ray(const TraceArgs& A, Ray& R) {
+  const float4 s0 = A.resume[2 * R.pix], s1 = A.resume[2 * R.pix + 1];
+  R.C[0] = s0.x; R.C[1] = s0.y; R.C[2] = s0.z;
+  R.T = s0.w;
+  R.first_id = __float_as_int(s1.x);
+  R.first_t = s1.y;
+  int x, y, z;
+  brick_coords(__float_as_uint(s1.z), A.g.log2nb, x, y, z);
+  R.vx = min(A.g.n - 1, max(0, x));
+  R.vy = min(A.g.n - 1, max(0, y));
+  R.vz = min(A.g.n - 1, max(0, z));
+  R.tcur = s1.w;
 }
 
 // The warp processes the pending voxel of lane `L`.
@@ -765,6 +788,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
             }
             R.pix = py * W + px;
             init_ray(A, R, (int)px, (int)py, true);
+            if (A.pix_list && A.resume) resume_ray(A, R);
             has = true;
           }
         }

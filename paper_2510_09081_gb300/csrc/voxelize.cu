@@ -193,6 +193,22 @@ __device__ __forceinline__ void flush_records(const GridDev& g, const unsigned l
   __syncwarp();
 }
 
+// Append a warp's staged culled records to cq (all lanes call); records past
+// the queue's capacity are counted but dropped, which sends the repair rounds
+// back to the full record stream.
+__device__ __forceinline__ void flush_culled(const GridDev& g, unsigned long long* cq,
+                                             const unsigned long long* srec, int n, int lane) {
+  if (n == 0) return;
+  uint32_t r0 = 0;
+  if (lane == 0) r0 = atomicAdd(&g.st->cq_cnt, (uint32_t)n);
+  r0 = __shfl_sync(FULLW, r0, 0);
+  for (int k = lane; k < n; k += 32) {
+    const uint32_t r = r0 + (uint32_t)k;
+    if (r < g.xq_cap) cq[r] = srec[k];
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
                                                const float4* __restrict__ nrm, long long V,
                                                GridDev g) {
@@ -305,28 +321,62 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t i) {
 
 // Pass 2: stream the fragment records; mode 0 lists every fragment, mode 1
 // those whose voxel the cull marked, mode 2 (repair) those whose voxel's
-// `need` bit is set.
+// `need` bit is set. Mode 1 also copies the records of unmarked voxels to the
+// (by then unused) exact-path queue, warp-staged, so that the repair rounds
+// stream only those; when they do not all fit, the repair streams every record.
 __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint32_t* __restrict__ need,
                                                  const uint32_t* __restrict__ pending) {
   if (mode == 2 && *pending == 0) return;
-  const uint32_t cnt = min(g.st->rec_cnt, g.rec_cap);
+  __shared__ unsigned long long s_rec[8][kWarpRecords];
+  unsigned long long* cq = reinterpret_cast<unsigned long long*>(g.xq);
+  const bool compact = mode == 2 && g.st->cq_cnt <= g.xq_cap;
+  const unsigned long long* src = compact ? cq : g.rec;
+  const uint32_t cnt = compact ? g.st->cq_cnt : min(g.st->rec_cnt, g.rec_cap);
   const uint32_t* sel = mode == 2 ? need : g.vis;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long* srec = s_rec[threadIdx.x >> 5];
+  int wcount = 0;  // culled records staged by this warp (mode 1, uniform)
   unsigned long long listed = 0;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-    const unsigned long long r = __ldcs(&g.rec[e]);
-    const uint32_t idx = (uint32_t)(r >> 32);
-    if (mode != 0 && !bit_set(sel, idx)) continue;
-    const uint32_t slot = atomicAdd(&g.cur[idx], 1u);
-    if (slot < g.list_cap) {
-      g.lists[slot] = (uint32_t)r;
-      ++listed;
-    } else {
-      set_err(g.st, kErrOverflow);
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t e0 = warp * 32; e0 < cnt; e0 += n_warps * 32) {
+    const uint32_t e = e0 + lane;
+    bool skip = true;
+    unsigned long long r = 0;
+    if (e < cnt) {
+      r = __ldcs(&src[e]);
+      const uint32_t idx = (uint32_t)(r >> 32);
+      skip = mode != 0 && !bit_set(sel, idx);
+      if (!skip) {
+        const uint32_t slot = atomicAdd(&g.cur[idx], 1u);
+        if (slot < g.list_cap) {
+          g.lists[slot] = (uint32_t)r;
+          ++listed;
+        } else {
+          set_err(g.st, kErrOverflow);
+        }
+      }
     }
+    if (mode == 1) {
+      const bool keep = e < cnt && skip;
+      const unsigned km = __ballot_sync(FULLW, keep);
+      if (keep) srec[wcount + __popc(km & lt)] = r;
+      wcount += __popc(km);
+      if (wcount > kWarpRecords - 32) {
+        __syncwarp();
+        flush_culled(g, cq, srec, wcount, lane);
+        wcount = 0;
+      }
+    }
+  }
+  if (mode == 1) {
+    __syncwarp();
+    flush_culled(g, cq, srec, wcount, lane);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) listed += __shfl_down_sync(FULLW, listed, o);
-  if ((threadIdx.x & 31) == 0 && listed) atomicAdd(&g.st->listed, listed);
+  if (lane == 0 && listed) atomicAdd(&g.st->listed, listed);
 }
 
 int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,

@@ -45,8 +45,8 @@ struct DevStatus {
   unsigned long long sum_count_field;  // checked by the scan
   unsigned long long sum_occ_field;
   unsigned long long listed;         // entries written by pass 2 and repairs
-  unsigned int xq_cnt;               // undecided (segment, voxel) pairs of the current pass
-  unsigned int xq_pad;
+  unsigned int xq_cnt;               // undecided (segment, voxel) pairs of pass 1
+  unsigned int cq_cnt;               // records of unlisted voxels pass 2 copied to xq
   unsigned int list_tail;            // next free list entry (scan total + repairs)
   unsigned int visible_voxels;
   unsigned int max_count;
@@ -74,6 +74,14 @@ __host__ __device__ __forceinline__ uint32_t brick_index(int x, int y, int z, in
   uint32_t b = ((uint32_t)(z >> 2) << (2 * log2nb)) | ((uint32_t)(y >> 2) << log2nb) |
                (uint32_t)(x >> 2);
   return (b << 6) | ((uint32_t)(z & 3) << 4) | ((uint32_t)(y & 3) << 2) | (uint32_t)(x & 3);
+}
+// Inverse of brick_index.
+__host__ __device__ __forceinline__ void brick_coords(uint32_t idx, int log2nb, int& x, int& y, int& z) {
+  const uint32_t b = idx >> 6, l = idx & 63u;
+  const uint32_t mask = (1u << log2nb) - 1u;
+  x = (int)(((b & mask) << 2) | (l & 3u));
+  y = (int)((((b >> log2nb) & mask) << 2) | ((l >> 2) & 3u));
+  z = (int)(((b >> (2 * log2nb)) << 2) | (l >> 4));
 }
 
 struct GridDev {
