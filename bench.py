@@ -145,6 +145,41 @@ def stage_bytes(stage, n, V, st, px):
     }[stage]
 
 
+# The trace kernel is bound by instruction issue and latency, not by DRAM: its
+# roofline counts the method's FP32 work, one ray-capsule entry test per list
+# entry a ray examines, against the FP32 rate of the SMs.
+TRACE_FLOPS_PER_ENTRY = 82        # FP32 operations of one capsule entry test
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+TRACE_SOURCES = ("paper_2510_09081_gb300/csrc/trace.cu", "paper_2510_09081_gb300/csrc/vrt_internal.cuh",
+                 "paper_2510_09081_gb300/csrc/launch.h")
+TRACE_PROFILE = os.path.join(ROOT, "profiles", "k_trace_tile_bundles_traffic.md")
+
+
+def trace_source_hash():
+    h = hashlib.sha256()
+    for f in TRACE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def trace_traffic():
+    """DRAM bytes per launch of the trace kernel from the committed ncu summary,
+    or None when the kernel's sources changed since it was captured."""
+    try:
+        fields = {}
+        for line in open(TRACE_PROFILE):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_hash") != trace_source_hash():
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def hbm_peak():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -284,6 +319,15 @@ def run_ours(args, rank, world, local_rank):
     h2d = int(upd_host[0][1].numel() * 4)
     d2h = int(rgba.numel() * 4)
 
+    # ---- one instrumented frame (not timed): list entries the rays examine
+    vrt.set_option(r.h, vrt.OPT_TRACE_COUNTERS, 1)
+    with torch.cuda.stream(stream):
+        frame(args.warmup)
+        vrt.sync(r.h)
+    entries = vrt.get_stats(r.h)["trace_entries"]
+    vrt.set_option(r.h, vrt.OPT_TRACE_COUNTERS, 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
     # ---- max over ranks
     vals = torch.tensor([mean_ms, statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
     if world > 1:
@@ -294,12 +338,13 @@ def run_ours(args, rank, world, local_rank):
         r.close()
         return None
     stages = {k: statistics.mean(v) for k, v in stage_ms.items() if v}
-    dom = max(stages, key=stages.get)
-    peak, peak_src = hbm_peak()
+    hbm, hbm_src = hbm_peak()
     px = cam.width * cam.height
-    B = stage_bytes(dom, ls.n, ls.n_vertices, st, px)
-    achieved = B / (stages[dom] * 1e-3) / 1e9
     frame_B = sum(stage_bytes(k, ls.n, ls.n_vertices, st, px) for k in stages)
+    # dominant kernel: the trace (one launch per frame, timed by the library's
+    # events on the grid's stream)
+    alu_peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = entries * TRACE_FLOPS_PER_ENTRY / (stages["trace"] * 1e-3) / 1e12
     srt = sorted(frame_ms)
     out = {
         "metric": METRIC,
@@ -326,12 +371,19 @@ def run_ours(args, rank, world, local_rank):
         "counters": {k: st[k] for k in ("fragments", "fragments_listed", "occupied_voxels",
                                         "visible_voxels", "repaired_voxels", "retraced_pixels",
                                         "exact_decisions", "max_count")},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-                     "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "k_trace_tile (trace stage)",
+                     "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / alu_peak, 4),
+                     "peak_source": (f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                     f"{SM_MAX_MHZ:.0f} MHz"),
+                     "work": (f"{entries} list entries examined x {TRACE_FLOPS_PER_ENTRY} FP32 ops "
+                              "(one ray-capsule entry test each)"),
+                     "traffic": trace_traffic(),
                      "frame_algorithmic_bytes": frame_B,
-                     "frame_frac": round(frame_B / (mean_ms * 1e-3) / 1e9 / peak, 4)},
+                     "frame_hbm_frac": round(frame_B / (mean_ms * 1e-3) / 1e9 / hbm, 4),
+                     "hbm_peak": hbm,
+                     "hbm_peak_source": (f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"
+                                         if hbm_src == "measured" else hbm_src)},
         "e2e": {"value": round(e2e_mean, 4), "unit": "ms/frame", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
