@@ -496,9 +496,9 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
 // The pending voxels of the warp's lanes with lists up to A.short_list
 // entries, processed together: their entries are numbered one after another
 // (lane by lane) and the warp takes 32 at a time, one (ray, entry) pair per
-// lane, so lanes with short lists do not wait for the longest one. Pairs that
-// pass the line-distance test are queued per warp in shared memory and get the
-// capsule test 32 at a time. A hit goes to its ray's slots in shared memory
+// lane (two such rounds per step), so lanes with short lists do not wait for
+// the longest one. Pairs that pass the line-distance test are queued per warp
+// in shared memory and get the capsule test 32 at a time. A hit goes to its ray's slots in shared memory
 // (the nearest key for an opaque ray; up to kRayKeys keys of a transparent
 // ray, sorted and composited by the ray's own lane afterwards). A transparent
 // ray with more hits in the voxel keeps its voxel pending for the whole-warp
@@ -557,26 +557,14 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       }
     }
   };
-  for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-    const uint32_t gq = t0 + lane;
+  auto owner = [&](uint32_t gq) {
     int j = 0;
 #pragma unroll
     for (int st = 16; st > 0; st >>= 1)
       if (__shfl_sync(FULL, incl, j + st - 1) <= gq) j += st;
-    j = min(j, 31);
-    const uint32_t fj = __shfl_sync(FULL, first, j);
-    bool pass = false;
-    uint32_t id = 0;
-    if (gq < total) {
-      id = __ldg(&A.g.lists[fj + gq]);
-      if (id + 1 >= A.n_vert) {
-        set_err(A.g.st, kErrBounds);
-      } else {
-        const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
-        const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
-        pass = lines_may_meet(f3(ro), f3(rd), f3(p0), f3(p1), rrm);
-      }
-    }
+    return min(j, 31);
+  };
+  auto append = [&](bool pass, uint32_t id, int j) {
     const unsigned m = __ballot_sync(FULL, pass);
     if (pass) q[qn + __popc(m & lt)] = make_uint2(id, (uint32_t)j);
     qn += __popc(m);
@@ -584,11 +572,37 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       __syncwarp();
       capsule_stage(32);
       __syncwarp();
-      // the pairs past the first 32 move to the front (reads 32.., writes ..31)
       if ((uint32_t)lane < qn - 32) q[lane] = q[32 + lane];
       __syncwarp();
       qn -= 32;
     }
+  };
+  // two independent (owner search, list load, vertex loads) chains per step:
+  // the loop is bound by their latency
+  for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+    const uint32_t ga = t0 + lane, gb = ga + 32;
+    const int ja = owner(ga), jb = owner(gb);
+    const uint32_t fa = __shfl_sync(FULL, first, ja), fb = __shfl_sync(FULL, first, jb);
+    const bool va = ga < total, vb = gb < total;
+    uint32_t ida = 0, idb = 0;
+    if (va) ida = __ldg(&A.g.lists[fa + ga]);
+    if (vb) idb = __ldg(&A.g.lists[fb + gb]);
+    const bool oka = va && ida + 1 < A.n_vert, okb = vb && idb + 1 < A.n_vert;
+    if ((va && !oka) || (vb && !okb)) set_err(A.g.st, kErrBounds);
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    if (oka) { a0 = __ldg(&A.pos[ida]); a1 = __ldg(&A.pos[ida + 1]); }
+    if (okb) { b0 = __ldg(&A.pos[idb]); b1 = __ldg(&A.pos[idb + 1]); }
+    bool pa = false, pb = false;
+    if (oka) {
+      const float4 ro = s_ray[0][wb + ja], rd = s_ray[1][wb + ja];
+      pa = lines_may_meet(f3(ro), f3(rd), f3(a0), f3(a1), rrm);
+    }
+    if (okb) {
+      const float4 ro = s_ray[0][wb + jb], rd = s_ray[1][wb + jb];
+      pb = lines_may_meet(f3(ro), f3(rd), f3(b0), f3(b1), rrm);
+    }
+    append(pa, ida, ja);
+    append(pb, idb, jb);
   }
   __syncwarp();
   capsule_stage(qn);
