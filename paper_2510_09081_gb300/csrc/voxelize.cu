@@ -255,6 +255,47 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     s_n[1][tid] = make_float4(n1.x, n1.y, n1.z, 0.0f);
   }
   __syncwarp();
+  // Candidates the first filter stage leaves undecided (a few percent) wait in
+  // a per-warp queue and get the Newton stage 32 at a time, so the warp does
+  // not run it for one or two lanes per step.
+  __shared__ uint2 s_uq[8][64];  // (owner lane, packed voxel)
+  uint2* uq = s_uq[threadIdx.x >> 5];
+  uint32_t un = 0;  // queued (uniform)
+  // a kept fragment: occupancy into the packed word, record staged (all lanes call)
+  auto emit = [&](bool keep, int j, const PackedWalk& p, int x, int y, int z) {
+    uint32_t idx = 0;
+    if (keep) {
+      idx = brick_index(x, y, z, g.log2nb);
+      const uint32_t clip = __float_as_uint(p.w3.z) >> 27;
+      add_fragment(g, f3(p.w0), f3(p.w1), f3(s_n[0][wb + j]), f3(s_n[1][wb + j]), clip & 1u,
+                   clip & 2u, x, y, z, F, sq);
+    }
+    const unsigned am = __ballot_sync(FULLW, keep);
+    if (keep) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | (uint32_t)(base + j);
+    wcount += __popc(am);
+    if (wcount > kWarpRecords - 32) {
+      __syncwarp();
+      flush_records(g, srec, wcount, lane);
+      wcount = 0;
+    }
+  };
+  // stage 2 for queued entries below cnt (all lanes call)
+  auto stage2 = [&](uint32_t cnt) {
+    int dec = 0, j = 0, x = 0, y = 0, z = 0;
+    PackedWalk p;
+    if ((uint32_t)lane < cnt) {
+      const uint2 it = uq[lane];
+      j = (int)it.x;
+      unpack_voxel(it.y, x, y, z);
+      p = s_w[wb + j];
+      dec = seg_stage2_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
+      if (dec < 0) {
+        queue_exact(g, (uint32_t)(base + j), x, y, z);
+        ++ex;
+      }
+    }
+    emit(dec > 0, j, p, x, y, z);
+  };
   for (uint32_t t0 = 0; t0 < total; t0 += 32) {
     const uint32_t gq = t0 + lane;
     int j = 0;
@@ -262,35 +303,35 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     for (int st = 16; st > 0; st >>= 1)
       if (__shfl_sync(FULLW, incl, j + st - 1) <= gq) j += st;
     j = min(j, 31);
-    const uint32_t seg = (uint32_t)(base + j);
     int x = 0, y = 0, z = 0, dec = 0;
     PackedWalk p;
     if (gq < total) {
       p = s_w[wb + j];
-      if (decode_candidate(p, g.n, gq - __float_as_uint(p.w3.w), x, y, z))
-        dec = g.force_exact ? -1 : seg_filter_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
+      if (decode_candidate(p, g.n, gq - __float_as_uint(p.w3.w), x, y, z)) {
+        if (g.force_exact) {
+          queue_exact(g, (uint32_t)(base + j), x, y, z);
+          ++ex;
+        } else {
+          dec = seg_stage1_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
+        }
+      }
     }
-    if (dec < 0) {
-      queue_exact(g, seg, x, y, z);
-      ++ex;
-    }
-    uint32_t idx = 0;
-    if (dec > 0) {
-      idx = brick_index(x, y, z, g.log2nb);
-      const uint32_t clip = __float_as_uint(p.w3.z) >> 27;
-      add_fragment(g, f3(p.w0), f3(p.w1), f3(s_n[0][wb + j]), f3(s_n[1][wb + j]), clip & 1u,
-                   clip & 2u, x, y, z, F, sq);
-    }
-    // stage the warp's records in shared memory; one global append per batch
-    const unsigned am = __ballot_sync(FULLW, dec > 0);
-    if (dec > 0) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg;
-    wcount += __popc(am);
-    if (wcount > kWarpRecords - 32) {
+    const unsigned um = __ballot_sync(FULLW, dec < 0);
+    if (dec < 0) uq[un + __popc(um & lt)] = make_uint2((uint32_t)j, pack_voxel(x, y, z));
+    un += __popc(um);
+    emit(dec > 0, j, p, x, y, z);
+    if (un >= 32) {
       __syncwarp();
-      flush_records(g, srec, wcount, lane);
-      wcount = 0;
+      stage2(32);
+      __syncwarp();
+      // entries past the first 32 move to the front (reads 32.., writes ..31)
+      if ((uint32_t)lane < un - 32) uq[lane] = uq[32 + lane];
+      __syncwarp();
+      un -= 32;
     }
   }
+  __syncwarp();
+  stage2(un);
   __syncwarp();
   flush_records(g, srec, wcount, lane);
   flush_counters(g.st, F, sq, ex);

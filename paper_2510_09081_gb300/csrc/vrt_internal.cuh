@@ -135,28 +135,41 @@ __device__ __forceinline__ float cmp3(float3 a, int k) { return k == 0 ? a.x : (
 // any t.
 // Both stages add a rounding allowance proportional to the squared magnitude
 // of the local coordinates.
-__device__ __forceinline__ int seg_box_filter(float3 a, float3 d, float rl) {
+// Rounding allowance of both stages for local coordinates a, a + d.
+__device__ __forceinline__ float seg_box_tol(float3 a, float3 d) {
   const float M = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fabsf(a.z)),
                         fmaxf(fmaxf(fabsf(a.x + d.x), fabsf(a.y + d.y)), fabsf(a.z + d.z)));
-  const float tol = 4.8e-7f * (M + 2.0f) * (M + 2.0f);
+  return 4.8e-7f * (M + 2.0f) * (M + 2.0f);
+}
+
+// Stage 1: 1 within, 0 not within, -1 undecided.
+__device__ __forceinline__ int seg_box_stage1(float3 a, float3 d, float rl) {
+  const float tol = seg_box_tol(a, d);
+  const float dd = dot3(d, d);
+  const float3 w = make_float3(0.5f - a.x, 0.5f - a.y, 0.5f - a.z);
+  const float t = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, __fdividef(dot3(w, d), dd))) : 0.0f;
+  const float3 e = w - t * d;  // c - p
+  const float ex = fmaxf(fabsf(e.x) - 0.5f, 0.0f), ey = fmaxf(fabsf(e.y) - 0.5f, 0.0f),
+              ez = fmaxf(fabsf(e.z) - 0.5f, 0.0f);
+  const float up2 = ex * ex + ey * ey + ez * ez;  // dist(p, box)^2
+  if (up2 + tol <= rl * rl) return 1;
+  const float e2 = dot3(e, e);
+  if (e2 > 0.0f) {
+    const float len = sqrtf(e2);
+    const float de = dot3(d, e);
+    const float reach = fmaxf(0.0f, fmaxf(-t * de, (1.0f - t) * de));
+    const float lb = len - __fdividef(0.5f * (fabsf(e.x) + fabsf(e.y) + fabsf(e.z)) + reach, len);
+    if (lb > rl && lb * lb - tol > rl * rl) return 0;
+  }
+  return -1;
+}
+
+// Stage 2: 1 within, 0 not within, -1 undecided (left to the exact decision).
+__device__ __forceinline__ int seg_box_stage2(float3 a, float3 d, float rl) {
+  const float tol = seg_box_tol(a, d);
   const float dd = dot3(d, d);
   const float3 w = make_float3(0.5f - a.x, 0.5f - a.y, 0.5f - a.z);
   float t = dd > 0.0f ? fminf(1.0f, fmaxf(0.0f, __fdividef(dot3(w, d), dd))) : 0.0f;
-  {
-    const float3 e = w - t * d;  // c - p
-    const float ex = fmaxf(fabsf(e.x) - 0.5f, 0.0f), ey = fmaxf(fabsf(e.y) - 0.5f, 0.0f),
-                ez = fmaxf(fabsf(e.z) - 0.5f, 0.0f);
-    const float up2 = ex * ex + ey * ey + ez * ez;  // dist(p, box)^2
-    if (up2 + tol <= rl * rl) return 1;
-    const float e2 = dot3(e, e);
-    if (e2 > 0.0f) {
-      const float len = sqrtf(e2);
-      const float de = dot3(d, e);
-      const float reach = fmaxf(0.0f, fmaxf(-t * de, (1.0f - t) * de));
-      const float lb = len - __fdividef(0.5f * (fabsf(e.x) + fabsf(e.y) + fabsf(e.z)) + reach, len);
-      if (lb > rl && lb * lb - tol > rl * rl) return 0;
-    }
-  }
   float f = 0.0f, g = 0.0f;
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
@@ -281,11 +294,15 @@ static __device__ __noinline__ bool seg_box_exact(const long long* A, const long
   return false;
 }
 
-// Filter decision for voxel (x, y, z): 1 within, 0 not, -1 undecided. a, b
-// are the snapped global endpoints (local coordinates are exact in fp32).
-__device__ __forceinline__ int seg_filter_at(float3 a, float3 b, int x, int y, int z, float rl) {
+// Filter stages for voxel (x, y, z): 1 within, 0 not, -1 undecided. a, b are
+// the snapped global endpoints (local coordinates are exact in fp32).
+__device__ __forceinline__ int seg_stage1_at(float3 a, float3 b, int x, int y, int z, float rl) {
   const float3 la = make_float3(a.x - (float)x, a.y - (float)y, a.z - (float)z);
-  return seg_box_filter(la, b - a, rl);
+  return seg_box_stage1(la, b - a, rl);
+}
+__device__ __forceinline__ int seg_stage2_at(float3 a, float3 b, int x, int y, int z, float rl) {
+  const float3 la = make_float3(a.x - (float)x, a.y - (float)y, a.z - (float)z);
+  return seg_box_stage2(la, b - a, rl);
 }
 
 // Exact decision for voxel (x, y, z) on the 2^-14 lattice.
