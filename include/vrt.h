@@ -138,7 +138,9 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
 
 /* Overwrite vertices [first_vertex, first_vertex + n_vertices) with new
  * coordinates (same topology); a dynamic frame's update. Same layout and
- * memory rules as vrt_upload_segments. */
+ * memory rules as vrt_upload_segments, except that coordinates (host or
+ * device) are checked on the device by the next vrt_voxelize: one outside
+ * [-256, 768) or not finite makes vrt_sync return VRT_ERR_INVALID_ARG. */
 vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_vertices,
                                const float* xyz, int32_t stride, int32_t on_device);
 

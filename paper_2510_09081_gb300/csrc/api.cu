@@ -114,22 +114,38 @@ GridDev gdev(vrt_grid g) {
   return d;
 }
 
+// Every coordinate finite and in [kCoordMin, kCoordMax). Accumulates without an
+// early exit so that the compiler vectorizes it (NaN fails both comparisons).
 bool host_coords_ok(const float* xyz, int stride, long long V) {
-  for (long long i = 0; i < V; ++i)
-    for (int k = 0; k < 3; ++k) {
-      const float x = xyz[i * stride + k];
-      if (!(x >= kCoordMin && x < kCoordMax)) return false;
+  unsigned bad = 0;
+  if (stride == 3) {
+    const long long m = 3 * V;
+    for (long long i = 0; i < m; ++i) {
+      const float x = xyz[i];
+      bad |= (unsigned)!(x >= kCoordMin) | (unsigned)!(x < kCoordMax);
     }
-  return true;
+  } else {
+    for (long long i = 0; i < V; ++i)
+      for (int k = 0; k < 3; ++k) {
+        const float x = xyz[i * stride + k];
+        bad |= (unsigned)!(x >= kCoordMin) | (unsigned)!(x < kCoordMax);
+      }
+  }
+  return bad == 0;
 }
 
 vrt_status copy_vertices(vrt_grid g, long long first, long long V, const float* xyz, int stride,
                          int on_device) {
   if (V == 0) return VRT_OK;
-  VRT_CUDA(g, cudaMemcpy2DAsync(g->raw + 3 * first, 3 * sizeof(float), xyz,
-                                (size_t)stride * sizeof(float), 3 * sizeof(float), (size_t)V,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (stride == 3) {  // contiguous rows: one plain copy
+    VRT_CUDA(g, cudaMemcpyAsync(g->raw + 3 * first, xyz, 3 * sizeof(float) * (size_t)V, kind,
                                 g->stream));
+  } else {
+    VRT_CUDA(g, cudaMemcpy2DAsync(g->raw + 3 * first, 3 * sizeof(float), xyz,
+                                  (size_t)stride * sizeof(float), 3 * sizeof(float), (size_t)V,
+                                  kind, g->stream));
+  }
   return VRT_OK;
 }
 
@@ -394,8 +410,8 @@ vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_verti
   if (first_vertex < 0 || n_vertices < 0 || first_vertex + n_vertices > g->V)
     return fail(g, VRT_ERR_INVALID_ARG, "vertex range outside the uploaded set");
   if (n_vertices > 0 && !xyz) return fail(g, VRT_ERR_INVALID_ARG, "xyz is NULL");
-  if (!on_device && !host_coords_ok(xyz, stride, n_vertices))
-    return fail(g, VRT_ERR_INVALID_ARG, "coordinates must be finite and in [-256, 768)");
+  // the per-frame path checks coordinates on the device (ingest), for host and
+  // device input alike; vrt_sync reports a bad one
   vrt_status s = copy_vertices(g, first_vertex, n_vertices, xyz, stride, on_device);
   if (s != VRT_OK) return s;
   g->stage = 1;

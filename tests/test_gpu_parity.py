@@ -276,6 +276,14 @@ def test_error_reporting():
         vrt.sync(r.h)
     assert e.value.status == vrt.ERR_INVALID_ARG
     vrt.sync(r.h)  # cleared
+    # a host update out of range: checked on the device, reported at sync
+    r.upload(ls.xyz, ls.offsets)
+    vrt.update_vertices(r.h, 0, np.ascontiguousarray(bad[:10]))
+    vrt.voxelize(r.h)
+    with pytest.raises(vrt.VrtError) as e:
+        vrt.sync(r.h)
+    assert e.value.status == vrt.ERR_INVALID_ARG
+    vrt.sync(r.h)  # cleared
     # trace before the list build
     r.upload(ls.xyz, ls.offsets)
     rgba = torch.zeros((4, 4, 4), device="cuda")
