@@ -76,6 +76,11 @@ def _load():
     lib.or_render.restype = i32
     lib.or_render.argtypes = [P, ctypes.POINTER(_Cam), ctypes.POINTER(_Params), i32, i64, i64,
                               P, P, P, P, P, P]
+    lib.or_voxel_fragments.restype = i64
+    lib.or_voxel_fragments.argtypes = [P, i64, i64, i64, P, i64, P]
+    lib.or_render_pixels.restype = i32
+    lib.or_render_pixels.argtypes = [P, ctypes.POINTER(_Cam), ctypes.POINTER(_Params), i32, P, i64,
+                                     P, P, P, P, P, P]
     lib.or_seg_box_within.restype = i32
     lib.or_seg_box_within.argtypes = [P, P, P, i64, i64]
     lib.or_clipped_capsule_sdf.restype = f64
@@ -216,6 +221,40 @@ class Oracle:
         lib.or_render(self._h, ctypes.byref(c), ctypes.byref(prm), int(bool(brute)),
                       int(pix_begin), int(pix_end), _ptr(rgba), _ptr(rgba_alt), _ptr(fid),
                       _ptr(fid_alt), _ptr(ft), _ptr(ex))
+        return dict(rgba=rgba, rgba_alt=rgba_alt, first_id=fid, first_id_alt=fid_alt,
+                    first_t=ft, exempt=ex)
+
+
+    # ------------------------------------------------------- sampled checks
+    def voxel_fragments(self, x, y, z):
+        """Segments listed in voxel (x, y, z) (increasing ids) and its occupancy
+        code sums (nominal, lowest, highest), by brute force over every segment."""
+        lib = _load()
+        occ = np.zeros(3, np.uint64)
+        n = int(lib.or_voxel_fragments(self._h, int(x), int(y), int(z), None, 0, _ptr(occ)))
+        ids = np.zeros(max(n, 1), np.uint32)
+        lib.or_voxel_fragments(self._h, int(x), int(y), int(z), _ptr(ids), n, _ptr(occ))
+        return ids[:n], tuple(int(v) for v in occ)
+
+    def render_pixels(self, cam, pix, alpha=1.0, ao_cones=0, brute=False, bands=None):
+        """Render the listed pixels (row-major indices); outputs as render()."""
+        lib = _load()
+        b = dict(DEFAULT_BANDS)
+        if bands:
+            b.update(bands)
+        prm = _Params(alpha=float(alpha), ao_cones=int(ao_cones), **b)
+        c = _cam(cam)
+        pix = np.ascontiguousarray(pix, np.int64)
+        n = pix.shape[0]
+        rgba = np.zeros((n, 4), np.float32)
+        rgba_alt = np.zeros((n, 4), np.float32)
+        fid = np.zeros(n, np.int32)
+        fid_alt = np.zeros(n, np.int32)
+        ft = np.zeros(n, np.float32)
+        ex = np.zeros(n, np.uint8)
+        lib.or_render_pixels(self._h, ctypes.byref(c), ctypes.byref(prm), int(bool(brute)),
+                             _ptr(pix), n, _ptr(rgba), _ptr(rgba_alt), _ptr(fid), _ptr(fid_alt),
+                             _ptr(ft), _ptr(ex))
         return dict(rgba=rgba, rgba_alt=rgba_alt, first_id=fid, first_id_alt=fid_alt,
                     first_t=ft, exempt=ex)
 

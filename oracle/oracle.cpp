@@ -29,6 +29,9 @@
 //                   pyramid).
 //   * brute      -- the same image from all segments, no lists (pin for the
 //                   conservativeness claim of Sec. 3.5).
+//   * sampled    -- one voxel's fragments (list and occupancy codes) and a list
+//                   of pixels, both by brute force over every segment, for
+//                   sampled checks of sets too large for a full list build.
 //
 // Parity bookkeeping: where an fp32 implementation could legitimately take the
 // other side of a near-tie (a grazing ray, a hit on a clip plane or the grid
@@ -66,14 +69,13 @@ inline V3 normalize(V3 a) { return (1.0 / norm(a)) * a; }
 inline double comp(V3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
 
 template <class F>
-void parallel_for(int64_t n, int nthreads, F fn) {
+void parallel_for(int64_t n, int nthreads, F fn, int64_t chunk = 64) {
   if (nthreads <= 1 || n < 2) {
     for (int64_t i = 0; i < n; ++i) fn(i);
     return;
   }
   std::atomic<int64_t> next(0);
   std::vector<std::thread> th;
-  const int64_t chunk = 64;
   for (int t = 0; t < nthreads; ++t)
     th.emplace_back([&]() {
       for (;;) {
@@ -326,6 +328,37 @@ struct Ctx {
 inline bool seg_valid(const Ctx& c, int64_t i) { return i + 1 < c.V && !c.last[i]; }
 
 // ------------------------------------------------------------ list building
+// Voxel range [vlo, vhi] (clamped) that can hold voxels within r_L of segment i.
+void seg_voxel_range(const Ctx& c, int64_t i, int64_t* vlo, int64_t* vhi) {
+  const int64_t* A = &c.X[3 * i];
+  const int64_t* B = &c.X[3 * (i + 1)];
+  for (int k = 0; k < 3; ++k) {
+    int64_t mn = std::min(A[k], B[k]) - c.RL, mx = std::max(A[k], B[k]) + c.RL;
+    vlo[k] = std::max<int64_t>(0, floordiv(mn, UNITS) - 1);
+    vhi[k] = std::min<int64_t>(c.N - 1, floordiv(mx, UNITS));
+  }
+}
+
+// Is voxel (x, y, z) within r_L of segment i (exact)? If so, its occupancy code
+// (Alg. 2/3 at the voxel centre, rounded to Q codes) and, where Q * occupancy
+// lies within 1e-3 of a rounding boundary, both neighbouring codes.
+bool fragment(const Ctx& c, int64_t i, int64_t x, int64_t y, int64_t z, uint32_t& qn,
+              uint32_t& ql, uint32_t& qh, bool& ambiguous) {
+  const int64_t lo[3] = {x * UNITS, y * UNITS, z * UNITS};
+  if (!seg_box_within(&c.X[3 * i], &c.X[3 * (i + 1)], lo, UNITS, c.RL)) return false;
+  V3 p = {x + 0.5, y + 0.5, z + 0.5};
+  double occ = capsule_occupancy(p, c.pos[i], c.pos[i + 1], c.nrm[i], c.nrm[i + 1], c.en[i],
+                                 c.en[i + 1], c.r, c.r_min);
+  double xq = (double)c.Q * occ;
+  double fl = std::floor(xq);
+  double fr = xq - fl;
+  qn = (uint32_t)std::floor(xq + 0.5);
+  ql = qn; qh = qn;
+  ambiguous = std::fabs(fr - 0.5) < 1e-3;
+  if (ambiguous) { ql = (uint32_t)fl; qh = (uint32_t)fl + 1; }
+  return true;
+}
+
 void build_lists(Ctx& c) {
   const int N = c.N;
   const int64_t nv = (int64_t)N * N * N;
@@ -333,32 +366,18 @@ void build_lists(Ctx& c) {
   struct SegOut { std::vector<uint32_t> vox; std::vector<uint32_t> qlo, qhi, qnom; };
   std::vector<SegOut> out(c.V);
   std::atomic<int64_t> amb(0);
-  const double Q = (double)c.Q;
   parallel_for(c.V, c.nthreads, [&](int64_t i) {
     if (!seg_valid(c, i)) return;
-    const int64_t* A = &c.X[3 * i];
-    const int64_t* B = &c.X[3 * (i + 1)];
     int64_t vlo[3], vhi[3];
-    for (int k = 0; k < 3; ++k) {
-      int64_t mn = std::min(A[k], B[k]) - c.RL, mx = std::max(A[k], B[k]) + c.RL;
-      vlo[k] = std::max<int64_t>(0, floordiv(mn, UNITS) - 1);
-      vhi[k] = std::min<int64_t>(N - 1, floordiv(mx, UNITS));
-    }
+    seg_voxel_range(c, i, vlo, vhi);
     SegOut& so = out[i];
     for (int64_t z = vlo[2]; z <= vhi[2]; ++z)
       for (int64_t y = vlo[1]; y <= vhi[1]; ++y)
         for (int64_t x = vlo[0]; x <= vhi[0]; ++x) {
-          int64_t lo[3] = {x * UNITS, y * UNITS, z * UNITS};
-          if (!seg_box_within(A, B, lo, UNITS, c.RL)) continue;
-          V3 p = {x + 0.5, y + 0.5, z + 0.5};
-          double occ = capsule_occupancy(p, c.pos[i], c.pos[i + 1], c.nrm[i], c.nrm[i + 1],
-                                         c.en[i], c.en[i + 1], c.r, c.r_min);
-          double xq = Q * occ;
-          double fl = std::floor(xq);
-          double fr = xq - fl;
-          uint32_t qn = (uint32_t)std::floor(xq + 0.5);
-          uint32_t ql = qn, qh = qn;
-          if (std::fabs(fr - 0.5) < 1e-3) { ql = (uint32_t)fl; qh = (uint32_t)fl + 1; amb++; }
+          uint32_t qn, ql, qh;
+          bool a;
+          if (!fragment(c, i, x, y, z, qn, ql, qh, a)) continue;
+          if (a) amb++;
           so.vox.push_back((uint32_t)((z * N + y) * N + x));
           so.qnom.push_back(qn); so.qlo.push_back(ql); so.qhi.push_back(qh);
         }
@@ -897,6 +916,79 @@ int32_t or_render(void* h, const or_camera* cam_in, const or_params* prm_in, int
     if (first_t) first_t[j] = po.t;
     if (exempt) exempt[j] = po.exempt;
   });
+  return 0;
+}
+
+// Fragments of one voxel by brute force over every segment (no list build): the
+// same exact predicate and codes as the list build, for sampled checks of sets
+// too large for a full build. Returns the count; writes up to `cap` ids in
+// increasing order and occ[0..2] = nominal, lowest and highest code sums.
+int64_t or_voxel_fragments(void* h, int64_t x, int64_t y, int64_t z, uint32_t* ids, int64_t cap,
+                           uint64_t* occ) {
+  Ctx* c = (Ctx*)h;
+  const int64_t n_chunks = 256;
+  const int64_t per = (c->V + n_chunks - 1) / n_chunks;
+  std::vector<std::vector<uint32_t>> found(n_chunks);
+  std::vector<uint64_t> on(n_chunks, 0), ol(n_chunks, 0), oh(n_chunks, 0);
+  parallel_for(n_chunks, c->nthreads, [&](int64_t k) {
+    for (int64_t i = k * per; i < std::min(c->V, (k + 1) * per); ++i) {
+      if (!seg_valid(*c, i)) continue;
+      int64_t vlo[3], vhi[3];
+      seg_voxel_range(*c, i, vlo, vhi);
+      if (x < vlo[0] || x > vhi[0] || y < vlo[1] || y > vhi[1] || z < vlo[2] || z > vhi[2]) continue;
+      uint32_t qn, ql, qh;
+      bool a;
+      if (!fragment(*c, i, x, y, z, qn, ql, qh, a)) continue;
+      found[k].push_back((uint32_t)i);
+      on[k] += qn; ol[k] += ql; oh[k] += qh;
+    }
+  }, 1);
+  int64_t n = 0;
+  uint64_t s0 = 0, s1 = 0, s2 = 0;
+  for (int64_t k = 0; k < n_chunks; ++k) {
+    for (uint32_t id : found[k]) {
+      if (ids && n < cap) ids[n] = id;
+      ++n;
+    }
+    s0 += on[k]; s1 += ol[k]; s2 += oh[k];
+  }
+  if (occ) { occ[0] = s0; occ[1] = s1; occ[2] = s2; }
+  return n;
+}
+
+// Render the n pixels listed in pix (row-major indices), one per thread, into
+// outputs indexed like pix.
+int32_t or_render_pixels(void* h, const or_camera* cam_in, const or_params* prm_in, int32_t brute,
+                         const int64_t* pix, int64_t n, float* rgba, float* rgba_alt,
+                         int32_t* first_id, int32_t* first_id_alt, float* first_t, uint8_t* exempt) {
+  Ctx* c = (Ctx*)h;
+  if (!brute && !c->have_lists) build_lists(*c);
+  if (prm_in->ao_cones && !c->have_mips) { if (!c->have_lists) build_lists(*c); build_mips(*c); }
+  Camera cam;
+  cam.width = cam_in->width; cam.height = cam_in->height; cam.ortho = cam_in->ortho;
+  for (int k = 0; k < 3; ++k) {
+    cam.eye[k] = cam_in->eye[k]; cam.target[k] = cam_in->target[k]; cam.up[k] = cam_in->up[k];
+  }
+  cam.fovy_deg = cam_in->fovy_deg; cam.ortho_h = cam_in->ortho_h;
+  Params prm;
+  prm.alpha = prm_in->alpha; prm.ao_cones = prm_in->ao_cones;
+  prm.tie_rel = prm_in->tie_rel; prm.tie_abs = prm_in->tie_abs;
+  prm.graze_rel = prm_in->graze_rel;
+  prm.pos_abs = prm_in->pos_abs; prm.pos_rel = prm_in->pos_rel;
+  parallel_for(n, c->nthreads, [&](int64_t j) {
+    const int64_t p = pix[j];
+    int px = (int)(p % cam.width), py = (int)(p / cam.width);
+    PixelOut po;
+    render_pixel(*c, cam, prm, px, py, brute != 0, po);
+    for (int k = 0; k < 4; ++k) {
+      if (rgba) rgba[4 * j + k] = po.rgba[k];
+      if (rgba_alt) rgba_alt[4 * j + k] = po.rgba_alt[k];
+    }
+    if (first_id) first_id[j] = po.id;
+    if (first_id_alt) first_id_alt[j] = po.id_alt;
+    if (first_t) first_t[j] = po.t;
+    if (exempt) exempt[j] = po.exempt;
+  }, 1);
   return 0;
 }
 

@@ -525,3 +525,34 @@ def test_ao_single_wall():
     # further from the wall is less occluded
     assert o.ao((13.0, 8.0, 8.0)) > ao
     assert full[0].sum() > 0
+
+
+# ------------------------------------------------------------- sampled queries
+def test_voxel_fragments_equal_the_list_build():
+    # the per-voxel brute-force query (for sets too large for a full build)
+    # against the full list build on a small set
+    ls = tiny_walks(n_lines=120, n_verts=30, seed=11)
+    o = oracle.Oracle.from_lineset(ls)
+    L = o.lists()
+    n = ls.n
+    rng = np.random.default_rng(3)
+    occupied = np.nonzero(L["count"])[0]
+    sample = np.concatenate([rng.choice(occupied, 40, replace=False), rng.integers(0, n ** 3, 10)])
+    for v in sample:
+        x, y, z = int(v % n), int((v // n) % n), int(v // (n * n))
+        ids, (qn, ql, qh) = o.voxel_fragments(x, y, z)
+        want = L["ids"][L["start"][v]:L["start"][v + 1]]
+        assert np.array_equal(ids, want), (x, y, z)
+        assert (qn, ql, qh) == (L["occ_nom"][v], L["occ_lo"][v], L["occ_hi"][v])
+
+
+@pytest.mark.parametrize("brute", [False, True])
+def test_render_pixels_equal_render(brute):
+    ls = tiny_walks(n_lines=200, n_verts=30, seed=12)
+    cam = tiny_walks_camera(width=40, height=30)
+    o = oracle.Oracle.from_lineset(ls)
+    full = o.render(cam, alpha=0.4, brute=brute)
+    pix = np.random.default_rng(5).choice(40 * 30, 60, replace=False)
+    part = o.render_pixels(cam, pix, alpha=0.4, brute=brute)
+    for k in ("rgba", "rgba_alt", "first_id", "first_id_alt", "first_t", "exempt"):
+        assert np.array_equal(part[k], full[k][pix]), k
