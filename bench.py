@@ -304,9 +304,13 @@ def run_ours(args, rank, world, local_rank):
     mean_ms = statistics.mean(frame_ms)
     launches = (st["kernel_launches"] - st0["kernel_launches"])
 
-    # ---- end-to-end through the C ABI with host buffers
+    # ---- end-to-end through the C ABI with host buffers (warmed up like the
+    # device frames: the first copy out of each pinned buffer maps it)
     e2e_ms = []
     with torch.cuda.stream(stream):
+        for f in range(max(args.warmup, n_upd)):
+            frame(f, host=True)
+        vrt.sync(r.h)
         for i in range(args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)

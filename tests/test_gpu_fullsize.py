@@ -104,3 +104,115 @@ def test_fullsize_culling_never_changes_the_image(frame):
     st = frame["stats"]
     assert st["visible_voxels"] < st["occupied_voxels"]
     assert st["repaired_voxels"] >= 0
+
+
+# --------------------------------------------------------------------------
+# Unsteady-flow pathlines: 1M particles x 32 vertices (31M segments) in the ABC
+# flow, 512^3 grid, radius 0.25, 1920x1080 from inside the domain, opaque,
+# six-cone AO, culling on. The oracle checks sampled voxels and, without AO,
+# sampled pixels by brute force; AO is checked against the oracle on the same
+# flow at 1/64 of the lines in a 128^3 grid (the same line density per voxel),
+# and at full size by properties: it leaves the first hits unchanged and only
+# darkens the colour.
+@pytest.fixture(scope="module")
+def abc_frame():
+    ls = G.abc_pathlines(frame=0)
+    cam = G.abc_camera(frame=0)
+    r = vrt.Renderer(ls.n, ls.radius)
+    r.upload(torch.from_numpy(ls.xyz).cuda(), ls.offsets)
+    out = dict(ls=ls, cam=cam, r=r)
+    rgba, fid, ft = r.frame(cam, alpha=1.0, ao_cones=6, cull_on=1)
+    vrt.sync(r.h)
+    out["ao"] = (rgba.cpu().numpy().reshape(-1, 4).copy(), fid.cpu().numpy().reshape(-1).copy(),
+                 ft.cpu().numpy().reshape(-1).copy())
+    out["words"] = vrt.read_grid(r.h, ls.n)
+    out["start"], out["len"], out["ids"] = vrt.read_lists(r.h, ls.n)
+    rgba, fid, ft = r.frame(cam, alpha=1.0, ao_cones=0, cull_on=1, voxelize_first=False)
+    vrt.sync(r.h)
+    out["plain"] = (rgba.cpu().numpy().reshape(-1, 4).copy(), fid.cpu().numpy().reshape(-1).copy(),
+                    ft.cpu().numpy().reshape(-1).copy())
+    out["oracle"] = oracle.Oracle.from_lineset(ls, nthreads=os.cpu_count() or 1)
+    yield out
+    r.close()
+    out["oracle"].close()
+
+
+def test_abc_fullsize_sampled_voxels(abc_frame):
+    ls, o = abc_frame["ls"], abc_frame["oracle"]
+    n = ls.n
+    rng = np.random.default_rng(20251011)
+    seg = rng.choice(ls.n_vertices - 1, 96, replace=False)
+    ok = np.diff(np.searchsorted(ls.offsets, [seg, seg + 1], side="right"), axis=0)[0] == 0
+    mid = 0.5 * (ls.xyz[seg[ok]] + ls.xyz[seg[ok] + 1])
+    vox = np.clip(np.floor(mid).astype(np.int64), 0, n - 1)[:32]
+    # most voxels are hidden from the camera inside the flow; voxels of
+    # segments just in front of the eye are seen, so they get lists
+    cam = abc_frame["cam"]
+    eye, f = np.array(cam.eye), np.array(cam.target) - np.array(cam.eye)
+    f /= np.linalg.norm(f)
+    m_all = 0.5 * (ls.xyz[:-1] + ls.xyz[1:])
+    rel = m_all - eye
+    near = np.nonzero((np.linalg.norm(rel, axis=1) < 6.0) & (rel @ f > 1.0))[0]
+    near = near[np.diff(np.searchsorted(ls.offsets, [near, near + 1], side="right"), axis=0)[0] == 0]
+    front = np.unique(np.floor(m_all[near]).astype(np.int64), axis=0)
+    front = front[rng.permutation(front.shape[0])[:24]]
+    vox = np.concatenate([vox, front, rng.integers(0, n, (8, 3))])
+    listed = 0
+    for x, y, z in vox:
+        ids, (_, lo, hi) = o.voxel_fragments(x, y, z)
+        v = (z * n + y) * n + x
+        w = int(abc_frame["words"][v])
+        assert (w & 0xFFFF) == ids.shape[0], (x, y, z)
+        assert lo <= (w >> 16) <= hi, (x, y, z, w >> 16, lo, hi)
+        ln = int(abc_frame["len"][v])
+        if ln:
+            assert ln == ids.shape[0], (x, y, z)
+            s = int(abc_frame["start"][v])
+            assert np.array_equal(np.sort(abc_frame["ids"][s:s + ln]), ids), (x, y, z)
+            listed += 1
+    assert listed >= 10
+
+
+def test_abc_fullsize_sampled_pixels_without_ao(abc_frame):
+    cam, o = abc_frame["cam"], abc_frame["oracle"]
+    pix = np.random.default_rng(8).choice(cam.width * cam.height, 128, replace=False)
+    ref = o.render_pixels(cam, pix, alpha=1.0, brute=True)
+    rgba, fid, ft = abc_frame["plain"]
+    res = compare_image(rgba[pix], fid[pix], ft[pix], ref)
+    assert res["col_bad"] == 0 and res["id_bad"] == 0, res
+    assert res["exempt_colour"] <= 0.01 * res["n"] and res["exempt_id"] <= 0.01 * res["n"], res
+    assert res["max_t_rel"] < 2e-4, res
+    assert res["hits"] >= 100, res
+
+
+def test_abc_fullsize_ao_properties(abc_frame):
+    rgba_ao, fid_ao, ft_ao = abc_frame["ao"]
+    rgba, fid, ft = abc_frame["plain"]
+    assert np.array_equal(fid_ao, fid) and np.array_equal(ft_ao, ft)
+    hit = fid >= 0
+    assert hit.sum() > 0.5 * fid.shape[0]
+    assert np.array_equal(rgba_ao[:, 3], rgba[:, 3])
+    assert (rgba_ao[:, :3] <= rgba[:, :3] + 1e-6).all() and (rgba_ao[:, :3] >= 0).all()
+    # the occluded interior must darken a good share of the hits
+    assert (rgba_ao[hit, :3].sum(1) < 0.95 * rgba[hit, :3].sum(1)).mean() > 0.2
+
+
+def test_abc_reduced_scale_ao_images():
+    ls = G.abc_pathlines(n_particles=15_625, n=128, frame=0)
+    cam = G.abc_camera(n=128, frame=0, width=320, height=180)
+    o = oracle.Oracle.from_lineset(ls, nthreads=os.cpu_count() or 1)
+    pix = np.random.default_rng(9).choice(cam.width * cam.height, 600, replace=False)
+    ref = o.render_pixels(cam, pix, alpha=1.0, ao_cones=6)
+    r = vrt.Renderer(ls.n, ls.radius)
+    r.upload(ls.xyz, ls.offsets)
+    rgba, fid, ft = r.frame(cam, alpha=1.0, ao_cones=6, cull_on=1)
+    vrt.sync(r.h)
+    rgba = rgba.cpu().numpy().reshape(-1, 4)
+    fid = fid.cpu().numpy().reshape(-1)
+    ft = ft.cpu().numpy().reshape(-1)
+    r.close()
+    o.close()
+    res = compare_image(rgba[pix], fid[pix], ft[pix], ref)
+    assert res["col_bad"] == 0 and res["id_bad"] == 0, res
+    assert res["exempt_colour"] <= 0.01 * res["n"] and res["exempt_id"] <= 0.01 * res["n"], res
+    assert res["hits"] >= 400, res
