@@ -254,6 +254,8 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         r.upload(xyz_dev, ls.offsets)
     vrt.set_option(r.h, vrt.OPT_STAGE_TIMING, 1)
+    vrt.set_option(r.h, vrt.OPT_MIPS_FORMAT, {"fp32": vrt.MIPS_F32, "fp16": vrt.MIPS_F16,
+                                              "bf16": vrt.MIPS_BF16}[args.mips])
     c = vrt.camera_c(cam)
     p = vrt.params_c(alpha=wl["alpha"], ao_cones=wl["ao"], cull=wl["cull"])
     rgba = torch.empty((cam.height, cam.width, 4), dtype=torch.float32, device=dev)
@@ -364,7 +366,8 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic",
         "impl": "ours",
-        "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else ""),
+        "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else "")
+                   + (f" [occupancy pyramid in {args.mips}]" if args.mips != "fp32" else ""),
                    "l2": "flushed between frames (512 MB write)",
                    "segments": ls.n_segments, "grid": ls.n, "pixels": px,
                    "p50_ms": round(srt[len(srt) // 2], 4),
@@ -434,6 +437,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mips", choices=("fp32", "fp16", "bf16"), default="fp32",
+                    help="storage of the occupancy pyramid (AO workloads)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="fraction of the bundle streamlines (small cases for profiler captures)")
     args = ap.parse_args()

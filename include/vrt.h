@@ -201,10 +201,19 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
  * VRT_OPT_STAGE_TIMING (2): value 1 records CUDA events on the grid's stream
  * around each stage (see vrt_get_stage_ms).
  * VRT_OPT_TRACE_COUNTERS (3): value 1 runs an instrumented trace that counts
- * its work into vrt_stats (slower; for analysis). */
+ * its work into vrt_stats (slower; for analysis).
+ * VRT_OPT_MIPS_FORMAT (4): storage of the occupancy pyramid texels, VRT_MIPS_F32
+ * (default), VRT_MIPS_F16 or VRT_MIPS_BF16; every level is averaged in fp32
+ * from its stored children and rounded to nearest once, and the trace widens
+ * the samples to fp32. Changing it invalidates the pyramid (vrt_build_mips
+ * again). vrt_read_mips returns the stored values widened to fp32. */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
 #define VRT_OPT_TRACE_COUNTERS 3
+#define VRT_OPT_MIPS_FORMAT 4
+#define VRT_MIPS_F32 0
+#define VRT_MIPS_F16 1
+#define VRT_MIPS_BF16 2
 vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value);
 
 /* Stage durations of the last frame in milliseconds (waits), measured with

@@ -24,6 +24,8 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "OOM", "OVERFLOW", "CUDA", "TIMEOUT", "STAT
 OPT_FORCE_EXACT = 1
 OPT_STAGE_TIMING = 2
 OPT_TRACE_COUNTERS = 3
+OPT_MIPS_FORMAT = 4
+MIPS_F32, MIPS_F16, MIPS_BF16 = 0, 1, 2
 STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
 
 # Exported symbols of the C ABI (include/vrt.h)

@@ -40,7 +40,8 @@ struct vrt_grid_s {
   unsigned long long* rec = nullptr;  // fragment records of pass 1 (list_cap entries)
   unsigned long long* tile_state = nullptr;
   uint32_t n_tiles = 0;
-  float* mips = nullptr;
+  void* mips = nullptr;            // occupancy pyramid (room for fp32 texels)
+  int mips_fmt = kMipsF32;
   long long lev_off[11] = {0};
   int n_levels = 0;
   uint32_t* vq[2] = {nullptr, nullptr};
@@ -116,6 +117,31 @@ GridDev gdev(vrt_grid g) {
 
 // Every coordinate finite and in [kCoordMin, kCoordMax). Accumulates without an
 // early exit so that the compiler vectorizes it (NaN fails both comparisons).
+// fp16 / bf16 bit patterns widened to fp32 (exact), for the test readback.
+float half_to_float(uint16_t h) {
+  const uint32_t s = (uint32_t)(h >> 15) << 31, e = (h >> 10) & 31u, m = h & 1023u;
+  float v;
+  if (e == 0) {
+    v = std::ldexp((float)m, -24);  // zero and subnormals
+  } else if (e == 31) {
+    v = m ? NAN : INFINITY;
+  } else {
+    v = std::ldexp((float)(m | 1024u), (int)e - 25);
+  }
+  uint32_t b;
+  std::memcpy(&b, &v, 4);
+  b |= s;
+  std::memcpy(&v, &b, 4);
+  return v;
+}
+
+float bf16_to_float(uint16_t h) {
+  const uint32_t b = (uint32_t)h << 16;
+  float v;
+  std::memcpy(&v, &b, 4);
+  return v;
+}
+
 bool host_coords_ok(const float* xyz, int stride, long long V) {
   unsigned bad = 0;
   if (stride == 3) {
@@ -444,9 +470,9 @@ vrt_status vrt_voxelize(vrt_grid g) {
 vrt_status vrt_build_mips(vrt_grid g) {
   if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
   if (g->stage < 2) return fail(g, VRT_ERR_STATE, "vrt_voxelize first");
-  if (!g->mips) VRT_CUDA(g, dalloc(&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  if (!g->mips) VRT_CUDA(g, dalloc((float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
   stage_mark(g, ST_MIPS, 0);
-  g->launches += launch_mips(gdev(g), g->mips, g->lev_off, g->n_levels, g->stream);
+  g->launches += launch_mips(gdev(g), g->mips, g->mips_fmt, g->lev_off, g->n_levels, g->stream);
   stage_mark(g, ST_MIPS, 1);
   VRT_CUDA(g, cudaGetLastError());
   g->mips_valid = true;
@@ -527,6 +553,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.count = g->trace_counters;
   a.alpha = p->alpha; a.ao = p->ao_cones ? 1 : 0;
   a.mips = g->mips;
+  a.mips_fmt = g->mips_fmt;
   for (int l = 0; l < 11; ++l) a.lev_off[l] = g->lev_off[l];
   a.n_levels = g->n_levels;
   a.rgba = reinterpret_cast<float4*>(rgba);
@@ -659,9 +686,16 @@ vrt_status vrt_read_lists(vrt_grid g, uint32_t* start, uint32_t* len, uint32_t* 
 vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats) {
   if (!g || !host) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
   if (!g->mips_valid) return fail(g, VRT_ERR_STATE, "vrt_build_mips first");
-  const uint64_t tot = (uint64_t)g->lev_off[g->n_levels - 1] + 1;
+  const uint64_t tot = std::min<uint64_t>((uint64_t)g->lev_off[g->n_levels - 1] + 1, n_floats);
   VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-  VRT_CUDA(g, cudaMemcpy(host, g->mips, std::min(tot, n_floats) * 4, cudaMemcpyDeviceToHost));
+  if (g->mips_fmt == kMipsF32) {
+    VRT_CUDA(g, cudaMemcpy(host, g->mips, tot * 4, cudaMemcpyDeviceToHost));
+    return VRT_OK;
+  }
+  std::vector<uint16_t> h(tot);
+  VRT_CUDA(g, cudaMemcpy(h.data(), g->mips, tot * 2, cudaMemcpyDeviceToHost));
+  for (uint64_t i = 0; i < tot; ++i) host[i] = g->mips_fmt == kMipsF16 ? half_to_float(h[i])
+                                                                       : bf16_to_float(h[i]);
   return VRT_OK;
 }
 
@@ -673,6 +707,13 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
   }
   if (option == VRT_OPT_TRACE_COUNTERS) {
     g->trace_counters = value ? 1 : 0;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_MIPS_FORMAT) {
+    if (value != VRT_MIPS_F32 && value != VRT_MIPS_F16 && value != VRT_MIPS_BF16)
+      return fail(g, VRT_ERR_INVALID_ARG, "mips format must be VRT_MIPS_F32, _F16 or _BF16");
+    if ((int)value != g->mips_fmt) g->mips_valid = false;
+    g->mips_fmt = (int)value;
     return VRT_OK;
   }
   if (option == VRT_OPT_STAGE_TIMING) {

@@ -29,7 +29,8 @@ struct TraceArgs {
   uint32_t n_vert;           // vertices; list entries must be < n_vert - 1
   float alpha;
   int ao;
-  const float* mips;
+  const void* mips;          // occupancy pyramid, texels in format mips_fmt
+  int mips_fmt;              // kMipsF32, kMipsF16 or kMipsBF16
   long long lev_off[11];
   int n_levels;
   float4* rgba;
@@ -65,8 +66,8 @@ int launch_scatter(const GridDev& g, int mode, const uint32_t* need, const uint3
 int launch_scan(const GridDev& g, int all_visible, unsigned long long* tile_state, uint32_t n_tiles,
                  cudaStream_t s);
 int launch_finalize(const GridDev& g, cudaStream_t s);
-int launch_mips(const GridDev& g, float* mips, const long long* lev_off, int n_levels,
-                 cudaStream_t s);
+int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off, int n_levels,
+                cudaStream_t s);
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
                 cudaStream_t s);
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);

@@ -40,6 +40,9 @@
 // no limit, the march queues every culled voxel before the point where it
 // ends; the voxels' hits could only end the ray sooner, so the next trace
 // of that pixel needs nothing more.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "launch.h"
 
 namespace vrt {
@@ -70,13 +73,17 @@ __device__ __forceinline__ float3 shfl3(float3 v, int src) {
 }
 
 // ------------------------------------------------ ambient occlusion (Sec 3.4)
-__device__ __forceinline__ float texel(const float* lev, int m, int x, int y, int z) {
+// Texel i of a pyramid level stored in format fmt, widened to fp32.
+__device__ __forceinline__ float texel(const void* lev, int fmt, int m, int x, int y, int z) {
   if ((unsigned)x >= (unsigned)m || (unsigned)y >= (unsigned)m || (unsigned)z >= (unsigned)m)
     return 0.0f;
-  return __ldg(&lev[((long long)z * m + y) * m + x]);
+  const long long i = ((long long)z * m + y) * m + x;
+  if (fmt == kMipsF16) return __half2float(__ldg((const __half*)lev + i));
+  if (fmt == kMipsBF16) return __bfloat162float(__ldg((const __nv_bfloat16*)lev + i));
+  return __ldg((const float*)lev + i);
 }
 
-__device__ __forceinline__ float trilinear(const float* lev, int m, float scale, float3 q) {
+__device__ __forceinline__ float trilinear(const void* lev, int fmt, int m, float scale, float3 q) {
   const float ux = q.x * scale - 0.5f, uy = q.y * scale - 0.5f, uz = q.z * scale - 0.5f;
   const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
   const int x = (int)fx0, y = (int)fy0, z = (int)fz0;
@@ -89,7 +96,7 @@ __device__ __forceinline__ float trilinear(const float* lev, int m, float scale,
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
         const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-        acc = fmaf(w, texel(lev, m, x + dx, y + dy, z + dz), acc);
+        acc = fmaf(w, texel(lev, fmt, m, x + dx, y + dy, z + dz), acc);
       }
   return acc;
 }
@@ -108,10 +115,12 @@ __device__ float cone_sample_clear(const TraceArgs& A, float3 P, int c, int k) {
   float3 q = P;
   const int ax = c >> 1;
   if (ax == 0) q.x += sg * t; else if (ax == 1) q.y += sg * t; else q.z += sg * t;
-  float s = trilinear(A.mips + A.lev_off[l0], A.g.n >> l0, 1.0f / (float)(1 << l0), q);
+  const int tb = A.mips_fmt == kMipsF32 ? 4 : 2;  // bytes per texel
+  const char* base = (const char*)A.mips;
+  float s = trilinear(base + tb * A.lev_off[l0], A.mips_fmt, A.g.n >> l0, 1.0f / (float)(1 << l0), q);
   if (fl > 0.0f && l0 + 1 <= maxl)
-    s = (1.0f - fl) * s +
-        fl * trilinear(A.mips + A.lev_off[l0 + 1], A.g.n >> (l0 + 1), 1.0f / (float)(2 << l0), q);
+    s = (1.0f - fl) * s + fl * trilinear(base + tb * A.lev_off[l0 + 1], A.mips_fmt, A.g.n >> (l0 + 1),
+                                         1.0f / (float)(2 << l0), q);
   return 1.0f - s;
 }
 

@@ -22,6 +22,7 @@ constexpr int kMaxRepairRounds = 4;
 constexpr uint32_t kRayQueueLimit = 8;          // culled voxels one ray queues per round
 constexpr uint32_t kShortList = 512;            // trace: longer lists go to the whole-warp path
 constexpr int kBrickDistMax = 15;               // cap of the empty-brick distance field
+constexpr int kMipsF32 = 0, kMipsF16 = 1, kMipsBF16 = 2;  // occupancy pyramid storage
 
 // per-vertex flag bits, stored in pos[i].w as raw bits
 constexpr uint32_t kFirst = 1u, kLast = 2u, kClipOn = 4u;

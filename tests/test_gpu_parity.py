@@ -230,6 +230,74 @@ def test_ambient_occlusion_images(alpha):
     assert_image(res, max_exempt_frac=0.02)
 
 
+# --------------------------------------- reduced-precision pyramid (FP16/BF16)
+# Each level is averaged in fp32 from its stored children and rounded once, so
+# level l of the stored pyramid lies within (l + 1) half-ulps of 1 (2^-12 for
+# fp16, 2^-9 for bf16; all texels are in [0, 1]) of the fp64 pyramid, beyond
+# the fp32 near-tie allowance. An AO sample is a convex combination of texels,
+# a cone's factor a product of four (1 - sample) terms in [0, 1] and AO their
+# mean, so a texel error e moves AO, and the composited colour, by at most 4 e.
+HALF_ULP = {vrt.MIPS_F16: 2.0 ** -12, vrt.MIPS_BF16: 2.0 ** -9}
+
+
+def _abc_small():
+    # the ABC flow at 1/64 of the benchmark's lines in a 128^3 grid: partial
+    # occlusion, so AO samples are neither 0 nor 1 and texels are not short
+    # binary fractions
+    from gen.linesets import abc_pathlines, abc_camera
+    return (abc_pathlines(n_particles=15_625, n=128, frame=0),
+            abc_camera(n=128, frame=0, width=320, height=180))
+
+
+@pytest.mark.parametrize("fmt", [vrt.MIPS_F16, vrt.MIPS_BF16])
+def test_reduced_precision_mips_match_oracle(fmt):
+    ls, _ = _abc_small()
+    n = ls.n
+    o = oracle.Oracle.from_lineset(ls)
+    L = o.lists()
+    ref = o.mips()
+    r = gpu_grid(ls)
+    vrt.set_option(r.h, vrt.OPT_MIPS_FORMAT, fmt)
+    vrt.voxelize(r.h)
+    vrt.build_mips(r.h)
+    got = vrt.read_mips(r.h, n)
+    r.close()
+    bound = ((L["occ_hi"].astype(np.float64) - L["occ_lo"]) / 32.0).reshape(n, n, n)
+    worst = []
+    for lvl, (g, f) in enumerate(zip(got, ref)):
+        err = np.abs(g - f) - bound
+        worst.append(float(err.max()))
+        assert err.max() <= (lvl + 1) * HALF_ULP[fmt] + 1e-6, (lvl, float(err.max()))
+        m = bound.shape[0] // 2
+        if m >= 1:
+            bound = bound.reshape(m, 2, m, 2, m, 2).mean(axis=(1, 3, 5))
+    assert max(worst) > 0.0  # the rounding is exercised
+    print(f"fmt {fmt}: max texel error per level {['%.1e' % w for w in worst]}")
+
+
+@pytest.mark.parametrize("fmt", [vrt.MIPS_F32, vrt.MIPS_F16, vrt.MIPS_BF16])
+def test_reduced_precision_ao_images(fmt):
+    ls, cam = _abc_small()
+    o = oracle.Oracle.from_lineset(ls)
+    pix = np.random.default_rng(9).choice(cam.width * cam.height, 1500, replace=False)
+    ref = o.render_pixels(cam, pix, alpha=1.0, ao_cones=6)
+    r = gpu_grid(ls)
+    vrt.set_option(r.h, vrt.OPT_MIPS_FORMAT, fmt)
+    rgba, fid, ft = gpu_image(r, cam, alpha=1.0, ao=6, cull=1)
+    r.close()
+    rgba, fid, ft = rgba.reshape(-1, 4)[pix], fid.reshape(-1)[pix], ft.reshape(-1)[pix]
+    levels = 6  # cone samples read levels 0..5 (diameter <= 2 * 9.5 * tan(half angle) < 32)
+    tol = RGBA_TOL + (4 * levels * HALF_ULP[fmt] if fmt != vrt.MIPS_F32 else 0.0)
+    res = compare_image(rgba, fid, ft, ref, tol=tol)
+    assert res["hits"] > 1000
+    assert_image(res, max_exempt_frac=0.02)
+    # the error actually seen, against the primary fp64 result (stated in the design doc)
+    ok = ((ref["exempt"] & 1) == 0) & (fid >= 0)
+    d = np.abs(rgba - ref["rgba"]).max(1)[ok]
+    print(f"fmt {fmt}: RGBA error vs fp64 oracle over {ok.sum()} hit pixels: "
+          f"mean {d.mean():.2e} max {d.max():.2e} (bound {tol:.1e})")
+
+
 # ------------------------------------------------------------ dynamic data
 def test_update_vertices_equals_fresh_upload():
     ls = tiny_walks(n_lines=500, n_verts=50, seed=1)
