@@ -216,6 +216,15 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
 #define VRT_MIPS_BF16 2
 vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value);
 
+/* Device memory the grid holds, in bytes (its buffers as currently sized). */
+vrt_status vrt_grid_device_bytes(vrt_grid g, uint64_t* bytes);
+
+/* Issue the grid's later work on another CUDA stream (NULL: the legacy default
+ * stream). Does not wait: the caller orders the switch, i.e. the grid's work
+ * issued so far must have finished, or be ordered before the new stream's work
+ * (an event), when the grid's next call runs. */
+vrt_status vrt_set_stream(vrt_grid g, void* cuda_stream);
+
 /* Stage durations of the last frame in milliseconds (waits), measured with
  * CUDA events on the grid's stream while VRT_OPT_STAGE_TIMING is on. Order:
  * 0 ingest, 1 voxelize pass 1, 2 mips, 3 cull marks, 4 scan, 5 voxelize
@@ -263,6 +272,79 @@ const char* vrt_last_error(vrt_grid g);
 
 /* Wait for the stream, free every device buffer and the handle. */
 vrt_status vrt_destroy(vrt_grid g);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop over resident line sets (continuous batching of frames).
+ * Line sets are registered once; a frame request names a set, an optional
+ * vertex update, a camera and render parameters, and a device output buffer.
+ * A scheduler thread issues requests as soon as a stream slot is free and the
+ * set has no frame in flight (frames of one set run in submission order; frames
+ * of different sets overlap on the device, one CUDA stream per slot). A set is
+ * resident on the device while its grid, lists and pyramid are allocated;
+ * admitting a frame of a non-resident set first evicts least-recently-used idle
+ * sets until its footprint fits the HBM budget (the server keeps a host copy of
+ * every set, updated by each issued frame, to upload it again). Each frame is
+ * exactly the frame of the plain calls on that set, so its result does not
+ * depend on what else runs. Latency is measured from vrt_server_submit to the
+ * host seeing the frame's stream work finish. Thread safety: submit, poll and
+ * stats may be called from any host threads. */
+typedef struct vrt_server_s* vrt_server;
+
+typedef struct {
+  uint64_t hbm_budget;  /* device bytes the resident sets may hold; 0 selects
+                           80% of the free device memory at creation */
+  int32_t max_inflight; /* frames on the device at once (stream slots), >= 1;
+                           0 selects 4 */
+  int32_t device;       /* CUDA device ordinal */
+} vrt_server_desc;
+
+typedef struct {
+  int64_t request_id;
+  int32_t set_id;
+  int32_t status;       /* the frame's vrt_status (vrt_sync of its grid) */
+  double latency_ms;    /* submit -> completion seen by the host */
+  double queue_ms;      /* submit -> issue */
+} vrt_server_result;
+
+typedef struct {
+  uint64_t hbm_budget;
+  uint64_t resident_bytes;   /* device bytes of the resident sets */
+  uint64_t completed;        /* requests finished so far */
+  int32_t resident_sets;
+  int32_t evictions;         /* sets evicted so far */
+  int32_t pending;           /* submitted, not yet issued */
+  int32_t inflight;          /* issued, not yet finished */
+} vrt_server_stats;
+
+vrt_status vrt_server_create(const vrt_server_desc* desc, vrt_server* out);
+
+/* Register a line set (host vertices, same layout and checks as
+ * vrt_upload_segments; copied). It is uploaded when a frame first needs it. */
+vrt_status vrt_server_add_set(vrt_server s, const vrt_grid_desc* grid, const float* xyz,
+                              int32_t stride, int64_t n_vertices, const int64_t* polyline_offsets,
+                              int64_t n_polylines, int32_t* set_id);
+
+/* Queue a frame of set `set_id`: vertices [first_vertex, first_vertex +
+ * n_vertices) take the HOST coordinates `xyz` (stride 3 or 4; copied at once;
+ * n_vertices may be 0), then voxelize, mips when cam params ask for AO, cull,
+ * trace into the DEVICE buffers rgba_out (width * height * 4 floats) and, when
+ * not NULL, first_id_out / first_t_out, which must stay valid until the
+ * request completes. Returns at once with its id. */
+vrt_status vrt_server_submit(vrt_server s, int32_t set_id, int64_t first_vertex,
+                             int64_t n_vertices, const float* xyz, int32_t stride,
+                             const vrt_camera* cam, const vrt_render_params* p, float* rgba_out,
+                             int32_t* first_id_out, float* first_t_out, int64_t* request_id);
+
+/* Move up to `cap` finished requests (in completion order) into `out`;
+ * *n_out = how many. With wait != 0, first waits until every submitted request
+ * has finished. */
+vrt_status vrt_server_poll(vrt_server s, vrt_server_result* out, int32_t cap, int32_t* n_out,
+                           int32_t wait);
+
+vrt_status vrt_server_get_stats(vrt_server s, vrt_server_stats* out);
+
+/* Waits for every submitted request, then frees the sets and the server. */
+vrt_status vrt_server_destroy(vrt_server s);
 
 #ifdef __cplusplus
 }

@@ -32,7 +32,9 @@ STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
 SYMBOLS = ["vrt_create_grid", "vrt_upload_segments", "vrt_update_vertices", "vrt_voxelize",
            "vrt_build_mips", "vrt_cull", "vrt_trace", "vrt_sync", "vrt_get_stats",
            "vrt_read_grid", "vrt_read_lists", "vrt_read_mips", "vrt_set_option",
-           "vrt_get_stage_ms", "vrt_scan_counts_noalloc", "vrt_last_error", "vrt_destroy"]
+           "vrt_get_stage_ms", "vrt_scan_counts_noalloc", "vrt_last_error", "vrt_destroy",
+           "vrt_grid_device_bytes", "vrt_set_stream", "vrt_server_create", "vrt_server_add_set",
+           "vrt_server_submit", "vrt_server_poll", "vrt_server_get_stats", "vrt_server_destroy"]
 
 
 class VrtError(RuntimeError):
@@ -44,6 +46,24 @@ class VrtError(RuntimeError):
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("radius", ctypes.c_float), ("r_min", ctypes.c_float),
                 ("occ_scale", ctypes.c_int32), ("max_fragments", ctypes.c_uint64)]
+
+
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("set_id", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("resident_sets", ctypes.c_int32),
+                ("evictions", ctypes.c_int32), ("pending", ctypes.c_int32),
+                ("inflight", ctypes.c_int32)]
 
 
 class CameraC(ctypes.Structure):
@@ -96,6 +116,16 @@ def load():
         "vrt_get_stage_ms": [P, P, i32],
         "vrt_scan_counts_noalloc": [P, P, P, u64, P, P, P],
         "vrt_destroy": [P],
+        "vrt_grid_device_bytes": [P, ctypes.POINTER(u64)],
+        "vrt_set_stream": [P, P],
+        "vrt_server_create": [ctypes.POINTER(ServerDesc), ctypes.POINTER(P)],
+        "vrt_server_add_set": [P, ctypes.POINTER(GridDesc), P, i32, i64, P, i64,
+                               ctypes.POINTER(i32)],
+        "vrt_server_submit": [P, i32, i64, i64, P, i32, ctypes.POINTER(CameraC),
+                              ctypes.POINTER(RenderParamsC), P, P, P, ctypes.POINTER(i64)],
+        "vrt_server_poll": [P, ctypes.POINTER(ServerResult), i32, ctypes.POINTER(i32), i32],
+        "vrt_server_get_stats": [P, ctypes.POINTER(ServerStats)],
+        "vrt_server_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -315,3 +345,84 @@ class Renderer:
         cull(self.h, c, p)
         trace(self.h, c, p, rgba, fid, ft)
         return rgba, fid, ft
+
+
+def grid_device_bytes(g) -> int:
+    out = ctypes.c_uint64(0)
+    _check(load().vrt_grid_device_bytes(g, ctypes.byref(out)), g)
+    return int(out.value)
+
+
+# ------------------------------------------------------------------- serving
+class Server:
+    """The library's request loop over resident line sets (vrt.h, "serving"):
+    ``submit`` queues a frame of a registered set and returns at once; ``poll``
+    returns finished requests with their status and latency."""
+
+    def __init__(self, hbm_budget=0, max_inflight=4, device=0):
+        desc = ServerDesc(hbm_budget=int(hbm_budget), max_inflight=int(max_inflight),
+                          device=int(device))
+        h = ctypes.c_void_p()
+        _check(load().vrt_server_create(ctypes.byref(desc), ctypes.byref(h)))
+        self.h = h
+
+    def add_set(self, xyz, offsets, n, radius, r_min=0.5, occ_scale=32, max_fragments=0) -> int:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        desc = GridDesc(n=int(n), radius=float(radius), r_min=float(r_min),
+                        occ_scale=int(occ_scale), max_fragments=int(max_fragments))
+        sid = ctypes.c_int32(0)
+        _check(load().vrt_server_add_set(self.h, ctypes.byref(desc), _ptr(xyz), int(xyz.shape[1]),
+                                         int(xyz.shape[0]), _ptr(offsets), int(offsets.shape[0] - 1),
+                                         ctypes.byref(sid)))
+        return int(sid.value)
+
+    def submit(self, set_id, cam, rgba, alpha=1.0, ao_cones=0, cull_on=0, first_id=None,
+               first_t=None, first_vertex=0, update=None) -> int:
+        """rgba (and first_id / first_t) are device tensors that must stay alive
+        until the request completes; update: host float32 [k, 3] for vertices
+        first_vertex .. first_vertex + k - 1."""
+        c = camera_c(cam)
+        p = params_c(alpha, ao_cones, cull_on, 0)
+        if update is None:
+            upd, n_upd, stride = None, 0, 3
+        else:
+            upd = np.ascontiguousarray(update, dtype=np.float32)
+            n_upd, stride = int(upd.shape[0]), int(upd.shape[1])
+        rid = ctypes.c_int64(0)
+        _check(load().vrt_server_submit(self.h, int(set_id), int(first_vertex), n_upd,
+                                        _ptr(upd) if upd is not None else None, stride,
+                                        ctypes.byref(c), ctypes.byref(p), _ptr(rgba),
+                                        _ptr(first_id) if first_id is not None else None,
+                                        _ptr(first_t) if first_t is not None else None,
+                                        ctypes.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, wait=False, cap=4096):
+        buf = (ServerResult * cap)()
+        n = ctypes.c_int32(0)
+        out = []
+        while True:
+            _check(load().vrt_server_poll(self.h, buf, cap, ctypes.byref(n), int(bool(wait))))
+            out += [dict(request_id=buf[i].request_id, set_id=buf[i].set_id, status=buf[i].status,
+                         latency_ms=buf[i].latency_ms, queue_ms=buf[i].queue_ms)
+                    for i in range(n.value)]
+            if n.value < cap:
+                return out
+            wait = False
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().vrt_server_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            _check(load().vrt_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

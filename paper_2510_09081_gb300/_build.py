@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvrt.so")
-SOURCES = ["api.cu", "ingest.cu", "voxelize.cu", "scan.cu", "mips.cu", "cull.cu", "trace.cu", "bricks.cu",
+SOURCES = ["api.cu", "ingest.cu", "voxelize.cu", "scan.cu", "mips.cu", "cull.cu", "trace.cu", "bricks.cu", "server.cu",
            "scan_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "launch.h"
@@ -62,6 +63,9 @@ struct vrt_grid_s {
   bool mips_valid = false;
   int culled = 0;
   std::string err;
+  // device memory held by this grid
+  std::unordered_map<void*, size_t> alloc_bytes;
+  uint64_t dev_bytes = 0;
 };
 
 std::string g_create_error;  // last error without a grid (creation, stand-alone calls)
@@ -84,16 +88,29 @@ vrt_status cuda_fail(vrt_grid g, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(g, e_, #call); \
   } while (0)
 
+// Device allocations of a grid, counted in g->dev_bytes.
 template <class T>
-cudaError_t dalloc(T** p, size_t count) {
+cudaError_t dalloc(vrt_grid g, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void**)p, count * sizeof(T));
+  const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) {
+    g->alloc_bytes[(void*)*p] = count * sizeof(T);
+    g->dev_bytes += count * sizeof(T);
+  }
+  return e;
 }
 
 template <class T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
+void dfree(vrt_grid g, T*& p) {
+  if (p) {
+    auto it = g->alloc_bytes.find((void*)p);
+    if (it != g->alloc_bytes.end()) {
+      g->dev_bytes -= it->second;
+      g->alloc_bytes.erase(it);
+    }
+    cudaFree(p);
+  }
   p = nullptr;
 }
 
@@ -255,9 +272,9 @@ vrt_status size_exact_queue(vrt_grid g) {
   want = std::min<unsigned long long>(want, 0xffffffffull);
   if (g->xq && g->xq_cap >= want) return VRT_OK;
   VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-  dfree(g->xq);
+  dfree(g, g->xq);
   g->xq_cap = 0;
-  VRT_CUDA(g, dalloc(&g->xq, (size_t)want));
+  VRT_CUDA(g, dalloc(g, &g->xq, (size_t)want));
   g->xq_cap = (uint32_t)want;
   return VRT_OK;
 }
@@ -266,13 +283,13 @@ void free_all(vrt_grid g) {
   for (int i = 0; i < VRT_N_STAGES; ++i)
     for (int j = 0; j < 2; ++j)
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
-  dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
-  dfree(g->word); dfree(g->cur); dfree(g->vis); dfree(g->bdist); dfree(g->btmp);
-  dfree(g->need); dfree(g->eroded); dfree(g->lists); dfree(g->tile_state);
-  dfree(g->xq); dfree(g->rec);
-  dfree(g->mips); dfree(g->vq[0]); dfree(g->vq[1]); dfree(g->pq[0]); dfree(g->pq[1]);
-  dfree(g->resume);
-  dfree(g->st);
+  dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm);
+  dfree(g, g->word); dfree(g, g->cur); dfree(g, g->vis); dfree(g, g->bdist); dfree(g, g->btmp);
+  dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->lists); dfree(g, g->tile_state);
+  dfree(g, g->xq); dfree(g, g->rec);
+  dfree(g, g->mips); dfree(g, g->vq[0]); dfree(g, g->vq[1]); dfree(g, g->pq[0]); dfree(g, g->pq[1]);
+  dfree(g, g->resume);
+  dfree(g, g->st);
 }
 
 }  // namespace
@@ -306,18 +323,18 @@ vrt_status vrt_create_grid(const vrt_grid_desc* desc, void* cuda_stream, vrt_gri
   const size_t nb = nv / 64;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  chk(dalloc(&g->word, nv));
-  chk(dalloc(&g->cur, nv));
-  chk(dalloc(&g->vis, nv / 32));
-  chk(dalloc(&g->need, nv / 32));
-  chk(dalloc(&g->bdist, nb));
-  chk(dalloc(&g->btmp, nb));
+  chk(dalloc(g, &g->word, nv));
+  chk(dalloc(g, &g->cur, nv));
+  chk(dalloc(g, &g->vis, nv / 32));
+  chk(dalloc(g, &g->need, nv / 32));
+  chk(dalloc(g, &g->bdist, nb));
+  chk(dalloc(g, &g->btmp, nb));
   g->n_tiles = (uint32_t)(nv / 4096);
-  chk(dalloc(&g->tile_state, g->n_tiles));
-  chk(dalloc(&g->st, 1));
+  chk(dalloc(g, &g->tile_state, g->n_tiles));
+  chk(dalloc(g, &g->st, 1));
   g->vq_cap = (uint32_t)nv;  // a voxel enters the repair queue at most once per list build
-  chk(dalloc(&g->vq[0], g->vq_cap));
-  chk(dalloc(&g->vq[1], g->vq_cap));
+  chk(dalloc(g, &g->vq[0], g->vq_cap));
+  chk(dalloc(g, &g->vq[1], g->vq_cap));
   if (e == cudaSuccess) chk(cudaMemsetAsync(g->st, 0, sizeof(DevStatus), g->stream));
   if (e == cudaSuccess) chk(cudaMemsetAsync(g->word, 0, nv * 4, g->stream));
   if (e == cudaSuccess) chk(cudaMemsetAsync(g->need, 0, nv / 8, g->stream));
@@ -362,12 +379,12 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
   const long long V = n_vertices;
   if (V > g->V_alloc) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-    dfree(g->raw); dfree(g->flags); dfree(g->pos); dfree(g->nrm);
+    dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm);
     g->V_alloc = 0;
-    VRT_CUDA(g, dalloc(&g->raw, 3 * (size_t)V + 6));
-    VRT_CUDA(g, dalloc(&g->flags, (size_t)V));
-    VRT_CUDA(g, dalloc(&g->pos, (size_t)V + 1));
-    VRT_CUDA(g, dalloc(&g->nrm, (size_t)V + 1));
+    VRT_CUDA(g, dalloc(g, &g->raw, 3 * (size_t)V + 6));
+    VRT_CUDA(g, dalloc(g, &g->flags, (size_t)V));
+    VRT_CUDA(g, dalloc(g, &g->pos, (size_t)V + 1));
+    VRT_CUDA(g, dalloc(g, &g->nrm, (size_t)V + 1));
     g->V_alloc = V;
   }
   // Default capacity: a tube of length L and list radius rl touches fewer than
@@ -404,11 +421,11 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
   cap = std::min<unsigned long long>(cap, 0xffffffffull);
   if (cap != g->list_cap || !g->lists) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-    dfree(g->lists);
-    dfree(g->rec);
+    dfree(g, g->lists);
+    dfree(g, g->rec);
     g->list_cap = 0;
-    VRT_CUDA(g, dalloc(&g->lists, (size_t)cap));
-    VRT_CUDA(g, dalloc(&g->rec, (size_t)cap));
+    VRT_CUDA(g, dalloc(g, &g->lists, (size_t)cap));
+    VRT_CUDA(g, dalloc(g, &g->rec, (size_t)cap));
     g->list_cap = cap;
   }
   {
@@ -470,7 +487,7 @@ vrt_status vrt_voxelize(vrt_grid g) {
 vrt_status vrt_build_mips(vrt_grid g) {
   if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
   if (g->stage < 2) return fail(g, VRT_ERR_STATE, "vrt_voxelize first");
-  if (!g->mips) VRT_CUDA(g, dalloc((float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  if (!g->mips) VRT_CUDA(g, dalloc(g, (float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
   stage_mark(g, ST_MIPS, 0);
   g->launches += launch_mips(gdev(g), g->mips, g->mips_fmt, g->lev_off, g->n_levels, g->stream);
   stage_mark(g, ST_MIPS, 1);
@@ -495,7 +512,7 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   VRT_CUDA(g, cudaMemsetAsync(g->tile_state, 0, (size_t)g->n_tiles * 8, g->stream));
   stage_mark(g, ST_CULL, 0);
   if (p->cull) {
-    if (!g->eroded) VRT_CUDA(g, dalloc(&g->eroded, nv));
+    if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
     g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->stream);
   } else {
     VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
@@ -537,11 +554,11 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   const uint32_t npx = (uint32_t)cam->width * (uint32_t)cam->height;
   if (g->culled && npx > g->pq_cap) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-    dfree(g->pq[0]); dfree(g->pq[1]); dfree(g->resume);
+    dfree(g, g->pq[0]); dfree(g, g->pq[1]); dfree(g, g->resume);
     g->pq_cap = 0;
-    VRT_CUDA(g, dalloc(&g->pq[0], npx));
-    VRT_CUDA(g, dalloc(&g->pq[1], npx));
-    VRT_CUDA(g, dalloc(&g->resume, 2 * (size_t)npx));
+    VRT_CUDA(g, dalloc(g, &g->pq[0], npx));
+    VRT_CUDA(g, dalloc(g, &g->pq[1], npx));
+    VRT_CUDA(g, dalloc(g, &g->resume, 2 * (size_t)npx));
     g->pq_cap = npx;
   }
   TraceArgs a;
@@ -696,6 +713,18 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats) {
   VRT_CUDA(g, cudaMemcpy(h.data(), g->mips, tot * 2, cudaMemcpyDeviceToHost));
   for (uint64_t i = 0; i < tot; ++i) host[i] = g->mips_fmt == kMipsF16 ? half_to_float(h[i])
                                                                        : bf16_to_float(h[i]);
+  return VRT_OK;
+}
+
+vrt_status vrt_grid_device_bytes(vrt_grid g, uint64_t* bytes) {
+  if (!g || !bytes) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  *bytes = g->dev_bytes;
+  return VRT_OK;
+}
+
+vrt_status vrt_set_stream(vrt_grid g, void* cuda_stream) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  g->stream = (cudaStream_t)cuda_stream;
   return VRT_OK;
 }
 

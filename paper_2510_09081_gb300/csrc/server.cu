@@ -1,0 +1,509 @@
+// Serving: a request loop over resident line sets (vrt.h, "serving").
+//
+// One scheduler thread owns the sets' grids and the stream slots. Submitting
+// threads only copy their request into pinned host memory and queue it. The
+// scheduler repeatedly (1) retires frames whose stream work has finished (a
+// host callback on the slot's stream flags them), (2) issues the oldest queued
+// request of every set that has no frame in flight, onto a free slot, making
+// its set resident first (evicting least-recently-used idle sets while the HBM
+// budget would be exceeded), and (3) sleeps until a submission or a finished
+// frame wakes it. CUDA work is issued with the lock released.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "vrt.h"
+
+extern std::string g_create_error;  // message returned by vrt_last_error(NULL)
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct ServerSet {
+  vrt_grid_desc desc{};
+  std::vector<float> xyz;        // host copy, 3 floats per vertex, kept current
+  std::vector<int64_t> offsets;
+  int64_t V = 0, P = 0;
+  vrt_grid grid = nullptr;
+  uint64_t bytes = 0;            // device bytes (measured once resident, else estimated)
+  bool busy = false;             // a frame in flight
+  uint64_t last_use = 0;
+};
+
+struct Request {
+  int64_t id = 0;
+  int32_t set = 0;
+  int64_t first = 0, n = 0;
+  float* upd = nullptr;          // pinned, 3 floats per vertex
+  size_t upd_cap = 0;
+  vrt_camera cam{};
+  vrt_render_params p{};
+  float* rgba = nullptr;
+  int32_t* first_id = nullptr;
+  float* first_t = nullptr;
+  Clock::time_point t_submit, t_issue;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  bool busy = false;
+  std::atomic<bool> done{false};
+  Clock::time_point t_done;
+  Request req;
+  struct vrt_server_s* server = nullptr;
+};
+
+}  // namespace
+
+struct vrt_server_s {
+  int device = 0;
+  uint64_t budget = 0;
+  uint64_t resident_bytes = 0;
+  std::vector<std::unique_ptr<ServerSet>> sets;
+  std::deque<Request> pending;
+  std::vector<std::unique_ptr<Slot>> slots;
+  std::deque<vrt_server_result> results;
+  std::multimap<size_t, float*> pinned_free;  // capacity (floats) -> buffer
+  std::vector<float*> pinned_all;
+  std::mutex mu;
+  std::condition_variable cv;     // wakes the scheduler
+  std::condition_variable cv_done;  // wakes waiters in poll / destroy
+  std::thread th;
+  bool stop = false;
+  int64_t next_id = 1;
+  uint64_t submitted = 0, completed = 0;
+  uint64_t tick = 0;
+  int evictions = 0;
+  int resident_sets = 0;
+  std::string err;
+};
+
+namespace {
+
+vrt_status sfail(vrt_server s, vrt_status st, const std::string& m) {
+  if (s) s->err = m;
+  g_create_error = m;
+  return st;
+}
+
+// Footprint estimate of a set before it has been resident (its measured size
+// replaces it afterwards): the grid's voxel arrays, vertex buffers, list and
+// record capacity, exact queue, pyramid, cull and repair scratch at 1080p.
+uint64_t estimate_bytes(const ServerSet& st) {
+  const uint64_t n = (uint64_t)st.desc.n, nv = n * n * n, V = (uint64_t)std::max<int64_t>(st.V, 1);
+  const double rl = st.desc.radius + 1.0 / 512.0;
+  double mean_len = 1.0;
+  {
+    double sum = 0;
+    int64_t cnt = 0;
+    for (int64_t p = 0; p < st.P; ++p)
+      for (int64_t i = st.offsets[p]; i + 1 < st.offsets[p + 1]; i += 64) {
+        const float* a = &st.xyz[3 * i];
+        const float* b = &st.xyz[3 * (i + 1)];
+        sum += std::sqrt((double)(b[0] - a[0]) * (b[0] - a[0]) + (double)(b[1] - a[1]) * (b[1] - a[1]) +
+                         (double)(b[2] - a[2]) * (b[2] - a[2]));
+        ++cnt;
+      }
+    if (cnt) mean_len = sum / cnt;
+  }
+  const double per = std::max(16.0, 0.9 * (mean_len + 2 * rl + 2) * (2 * rl + 2) * (2 * rl + 2));
+  const uint64_t cap = st.desc.max_fragments ? st.desc.max_fragments : (uint64_t)(per * V);
+  const uint64_t xq = std::max<uint64_t>(4 * V, 1ull << 22);
+  return nv * 17 + nv / 4 + V * 45 + cap * 12 + xq * 8 + nv * 5 + 2073600ull * 40;
+}
+
+void CUDART_CB on_frame_done(void* arg) {
+  Slot* sl = (Slot*)arg;
+  sl->t_done = Clock::now();
+  sl->done.store(true);
+  std::lock_guard<std::mutex> lk(sl->server->mu);
+  sl->server->cv.notify_all();
+}
+
+// Make set `k` resident: evict idle sets (least recently used first) while the
+// budget would be exceeded, then create and upload it. Scheduler thread, called
+// with the lock held; releases it around the CUDA calls. Returns false when it
+// does not fit yet (busy sets hold the memory) or on an error (*st_out).
+bool make_resident(vrt_server s, std::unique_lock<std::mutex>& lk, int k, vrt_status* st_out) {
+  ServerSet& st = *s->sets[k];
+  *st_out = VRT_OK;
+  if (st.grid) return true;
+  if (!st.bytes) st.bytes = estimate_bytes(st);
+  while (s->resident_bytes + st.bytes > s->budget) {
+    int victim = -1;
+    for (size_t i = 0; i < s->sets.size(); ++i) {
+      const ServerSet& o = *s->sets[i];
+      if (o.grid && !o.busy && (victim < 0 || o.last_use < s->sets[victim]->last_use)) victim = (int)i;
+    }
+    if (victim < 0) {
+      if (s->resident_bytes == 0) break;  // alone: try, its measured size decides
+      return false;                       // else wait for busy sets
+    }
+    ServerSet& v = *s->sets[victim];
+    vrt_grid vg = v.grid;
+    v.grid = nullptr;
+    s->resident_bytes -= v.bytes;
+    --s->resident_sets;
+    ++s->evictions;
+    lk.unlock();
+    vrt_destroy(vg);
+    lk.lock();
+  }
+  s->resident_bytes += st.bytes;  // reserved while it is created
+  ++s->resident_sets;
+  lk.unlock();
+  vrt_grid g = nullptr;
+  vrt_status r = vrt_create_grid(&st.desc, nullptr, &g);
+  if (r == VRT_OK) r = vrt_upload_segments(g, st.xyz.data(), 3, st.V, st.offsets.data(), st.P, 0);
+  if (r != VRT_OK && g) {
+    vrt_destroy(g);
+    g = nullptr;
+  }
+  uint64_t b = 0;
+  if (r == VRT_OK) vrt_grid_device_bytes(g, &b);
+  lk.lock();
+  if (r == VRT_OK) {  // the measured size replaces the estimate
+    s->resident_bytes += b - st.bytes;
+    st.bytes = b;
+    if (b > s->budget) {  // alone it exceeds the budget
+      lk.unlock();
+      vrt_destroy(g);
+      lk.lock();
+      r = VRT_ERR_OOM;
+    }
+  }
+  if (r != VRT_OK) {
+    s->resident_bytes -= st.bytes;
+    --s->resident_sets;
+    *st_out = r;
+    return false;
+  }
+  st.grid = g;
+  return true;
+}
+
+// Evict idle sets (least recently used first) while the resident sets hold
+// more than the budget (buffers sized by a frame can grow a set). Lock held;
+// released around the CUDA calls.
+void trim(vrt_server s, std::unique_lock<std::mutex>& lk) {
+  while (s->resident_bytes > s->budget) {
+    int victim = -1;
+    for (size_t i = 0; i < s->sets.size(); ++i) {
+      const ServerSet& o = *s->sets[i];
+      if (o.grid && !o.busy && (victim < 0 || o.last_use < s->sets[victim]->last_use)) victim = (int)i;
+    }
+    if (victim < 0) return;
+    ServerSet& v = *s->sets[victim];
+    vrt_grid vg = v.grid;
+    v.grid = nullptr;
+    s->resident_bytes -= v.bytes;
+    --s->resident_sets;
+    ++s->evictions;
+    lk.unlock();
+    vrt_destroy(vg);
+    lk.lock();
+  }
+}
+
+// Issue one frame of `rq` on slot `sl` (scheduler thread, lock released).
+vrt_status issue(vrt_server s, Slot& sl, Request& rq) {
+  ServerSet& st = *s->sets[rq.set];
+  vrt_grid g = st.grid;
+  vrt_status r = vrt_set_stream(g, sl.stream);
+  if (r == VRT_OK && rq.n > 0) {
+    // the host copy follows every issued update (for uploads after an eviction)
+    std::memcpy(&st.xyz[3 * rq.first], rq.upd, sizeof(float) * 3 * (size_t)rq.n);
+    r = vrt_update_vertices(g, rq.first, rq.n, rq.upd, 3, 0);
+  }
+  if (r == VRT_OK) r = vrt_voxelize(g);
+  if (r == VRT_OK && rq.p.ao_cones) r = vrt_build_mips(g);
+  if (r == VRT_OK) r = vrt_cull(g, &rq.cam, &rq.p);
+  if (r == VRT_OK) r = vrt_trace(g, &rq.cam, &rq.p, rq.rgba, rq.first_id, rq.first_t);
+  if (r == VRT_OK && cudaLaunchHostFunc(sl.stream, on_frame_done, &sl) != cudaSuccess)
+    r = VRT_ERR_CUDA;
+  return r;
+}
+
+void finish(vrt_server s, const Request& rq, int32_t status, Clock::time_point t_done) {  // lock held
+  vrt_server_result res;
+  res.request_id = rq.id;
+  res.set_id = rq.set;
+  res.status = status;
+  res.latency_ms = ms_between(rq.t_submit, t_done);
+  res.queue_ms = ms_between(rq.t_submit, rq.t_issue);
+  s->results.push_back(res);
+  if (rq.upd) s->pinned_free.emplace(rq.upd_cap, rq.upd);
+  ++s->completed;
+  s->cv_done.notify_all();
+}
+
+void scheduler(vrt_server s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    // (1) retire finished frames
+    for (auto& slp : s->slots) {
+      Slot& sl = *slp;
+      if (!sl.busy || !sl.done.load()) continue;
+      ServerSet& st = *s->sets[sl.req.set];
+      lk.unlock();
+      const vrt_status status = vrt_sync(st.grid);  // the frame's device status
+      uint64_t b = 0;
+      vrt_grid_device_bytes(st.grid, &b);
+      lk.lock();
+      s->resident_bytes += b - st.bytes;  // lazily sized buffers may have grown
+      st.bytes = b;
+      st.busy = false;
+      sl.busy = false;
+      sl.done.store(false);
+      finish(s, sl.req, status, sl.t_done);
+    }
+    trim(s, lk);
+    // (2) issue: the oldest queued request of each idle set, while slots are free
+    bool issued = false;
+    std::vector<char> blocked(s->sets.size(), 0);  // no room for the set this round
+    for (;;) {
+      Slot* free_slot = nullptr;
+      for (auto& slp : s->slots)
+        if (!slp->busy) { free_slot = slp.get(); break; }
+      if (!free_slot) break;
+      // the first request that is the oldest of its set, whose set is idle and not blocked
+      std::vector<char> seen(s->sets.size(), 0);
+      size_t pick = s->pending.size();
+      for (size_t i = 0; i < s->pending.size(); ++i) {
+        const int k = s->pending[i].set;
+        if (seen[k]) continue;
+        seen[k] = 1;
+        if (!s->sets[k]->busy && !blocked[k]) { pick = i; break; }
+      }
+      if (pick == s->pending.size()) break;
+      Request rq = s->pending[pick];
+      s->pending.erase(s->pending.begin() + (long)pick);
+      ServerSet& st = *s->sets[rq.set];
+      st.busy = true;
+      st.last_use = ++s->tick;
+      free_slot->busy = true;
+      free_slot->done.store(false);
+      vrt_status r = VRT_OK;
+      const bool ok = make_resident(s, lk, rq.set, &r);
+      if (!ok && r == VRT_OK) {  // no room yet: back in place, try again later
+        st.busy = false;
+        free_slot->busy = false;
+        s->pending.insert(s->pending.begin() + (long)pick, rq);
+        blocked[rq.set] = 1;
+        continue;
+      }
+      if (ok) {
+        rq.t_issue = Clock::now();
+        free_slot->req = rq;
+        lk.unlock();
+        r = issue(s, *free_slot, free_slot->req);
+        lk.lock();
+      }
+      if (r != VRT_OK) {  // failed before reaching the device
+        st.busy = false;
+        free_slot->busy = false;
+        rq.t_issue = Clock::now();
+        finish(s, rq, r, Clock::now());
+      }
+      issued = true;
+    }
+    bool inflight = false;
+    for (auto& slp : s->slots) inflight = inflight || slp->busy;
+    if (s->stop && s->pending.empty() && !inflight) break;
+    if (!issued) s->cv.wait_for(lk, std::chrono::milliseconds(2));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+vrt_status vrt_server_create(const vrt_server_desc* desc, vrt_server* out) {
+  if (!out || !desc) return sfail(nullptr, VRT_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (desc->max_inflight < 0) return sfail(nullptr, VRT_ERR_INVALID_ARG, "max_inflight must be >= 0");
+  vrt_server s = new (std::nothrow) vrt_server_s();
+  if (!s) return sfail(nullptr, VRT_ERR_OOM, "host allocation failed");
+  s->device = desc->device;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(s->device) != cudaSuccess) {
+    delete s;
+    return sfail(nullptr, VRT_ERR_INVALID_ARG, "bad device");
+  }
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  s->budget = desc->hbm_budget ? desc->hbm_budget : (uint64_t)(0.8 * (double)fr);
+  const int slots = desc->max_inflight ? desc->max_inflight : 4;
+  for (int i = 0; i < slots; ++i) {
+    auto sl = std::make_unique<Slot>();
+    sl->server = s;
+    if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto& o : s->slots) cudaStreamDestroy(o->stream);
+      delete s;
+      cudaSetDevice(prev);
+      return sfail(nullptr, VRT_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    s->slots.push_back(std::move(sl));
+  }
+  cudaSetDevice(prev);
+  s->th = std::thread(scheduler, s);
+  *out = s;
+  return VRT_OK;
+}
+
+vrt_status vrt_server_add_set(vrt_server s, const vrt_grid_desc* grid, const float* xyz,
+                              int32_t stride, int64_t n_vertices, const int64_t* offsets,
+                              int64_t n_polylines, int32_t* set_id) {
+  if (!s || !grid || !offsets || !set_id || (n_vertices > 0 && !xyz))
+    return sfail(s, VRT_ERR_INVALID_ARG, "NULL argument");
+  if (stride != 3 && stride != 4) return sfail(s, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  if (n_vertices < 0 || n_polylines < 0 || offsets[0] != 0 || offsets[n_polylines] != n_vertices)
+    return sfail(s, VRT_ERR_INVALID_ARG, "offsets must start at 0 and end at n_vertices");
+  auto st = std::make_unique<ServerSet>();
+  st->desc = *grid;
+  st->V = n_vertices;
+  st->P = n_polylines;
+  st->offsets.assign(offsets, offsets + n_polylines + 1);
+  st->xyz.resize(3 * (size_t)n_vertices);
+  for (int64_t i = 0; i < n_vertices; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const float x = xyz[i * stride + k];
+      if (!(x >= -256.0f && x < 768.0f))
+        return sfail(s, VRT_ERR_INVALID_ARG, "coordinates must be finite and in [-256, 768)");
+      st->xyz[3 * i + k] = x;
+    }
+  std::lock_guard<std::mutex> lk(s->mu);
+  st->bytes = 0;
+  s->sets.push_back(std::move(st));
+  *set_id = (int32_t)s->sets.size() - 1;
+  return VRT_OK;
+}
+
+vrt_status vrt_server_submit(vrt_server s, int32_t set_id, int64_t first_vertex,
+                             int64_t n_vertices, const float* xyz, int32_t stride,
+                             const vrt_camera* cam, const vrt_render_params* p, float* rgba_out,
+                             int32_t* first_id_out, float* first_t_out, int64_t* request_id) {
+  const Clock::time_point t0 = Clock::now();
+  if (!s || !cam || !p || !rgba_out || !request_id) return sfail(s, VRT_ERR_INVALID_ARG, "NULL argument");
+  if (stride != 3 && stride != 4) return sfail(s, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  Request rq;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return sfail(s, VRT_ERR_STATE, "server is shutting down");
+    if (set_id < 0 || set_id >= (int32_t)s->sets.size())
+      return sfail(s, VRT_ERR_INVALID_ARG, "unknown set");
+    const ServerSet& st = *s->sets[set_id];
+    if (first_vertex < 0 || n_vertices < 0 || first_vertex + n_vertices > st.V || (n_vertices > 0 && !xyz))
+      return sfail(s, VRT_ERR_INVALID_ARG, "vertex range outside the set");
+    if (n_vertices > 0) {  // a pooled pinned buffer large enough, if any
+      auto it = s->pinned_free.lower_bound(3 * (size_t)n_vertices);
+      if (it != s->pinned_free.end()) {
+        rq.upd_cap = it->first;
+        rq.upd = it->second;
+        s->pinned_free.erase(it);
+      }
+    }
+  }
+  if (n_vertices > 0) {
+    if (!rq.upd) {
+      rq.upd_cap = 3 * (size_t)n_vertices;
+      int prev = 0;
+      cudaGetDevice(&prev);
+      cudaSetDevice(s->device);
+      void* h = nullptr;
+      const cudaError_t e = cudaMallocHost(&h, rq.upd_cap * sizeof(float));
+      cudaSetDevice(prev);
+      if (e != cudaSuccess) return sfail(s, VRT_ERR_OOM, "cudaMallocHost failed");
+      rq.upd = (float*)h;
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->pinned_all.push_back(rq.upd);
+    }
+    for (int64_t i = 0; i < n_vertices; ++i)
+      for (int k = 0; k < 3; ++k) rq.upd[3 * i + k] = xyz[i * stride + k];
+  }
+  rq.set = set_id;
+  rq.first = first_vertex;
+  rq.n = n_vertices;
+  rq.cam = *cam;
+  rq.p = *p;
+  rq.rgba = rgba_out;
+  rq.first_id = first_id_out;
+  rq.first_t = first_t_out;
+  rq.t_submit = t0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  rq.id = s->next_id++;
+  *request_id = rq.id;
+  s->pending.push_back(rq);
+  ++s->submitted;
+  s->cv.notify_all();
+  return VRT_OK;
+}
+
+vrt_status vrt_server_poll(vrt_server s, vrt_server_result* out, int32_t cap, int32_t* n_out,
+                           int32_t wait) {
+  if (!s || !n_out || (cap > 0 && !out)) return sfail(s, VRT_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (wait) s->cv_done.wait(lk, [&] { return s->completed == s->submitted; });
+  int32_t n = 0;
+  while (n < cap && !s->results.empty()) {
+    out[n++] = s->results.front();
+    s->results.pop_front();
+  }
+  *n_out = n;
+  return VRT_OK;
+}
+
+vrt_status vrt_server_get_stats(vrt_server s, vrt_server_stats* out) {
+  if (!s || !out) return sfail(s, VRT_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->hbm_budget = s->budget;
+  out->resident_bytes = s->resident_bytes;
+  out->completed = s->completed;
+  out->evictions = s->evictions;
+  out->pending = (int32_t)s->pending.size();
+  int inflight = 0;
+  for (auto& sl : s->slots) inflight += sl->busy ? 1 : 0;
+  out->inflight = inflight;
+  out->resident_sets = s->resident_sets;
+  return VRT_OK;
+}
+
+vrt_status vrt_server_destroy(vrt_server s) {
+  if (!s) return sfail(nullptr, VRT_ERR_INVALID_ARG, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->th.joinable()) s->th.join();
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  for (auto& st : s->sets)
+    if (st->grid) vrt_destroy(st->grid);
+  for (auto& sl : s->slots) cudaStreamDestroy(sl->stream);
+  for (float* p : s->pinned_all) cudaFreeHost(p);
+  cudaSetDevice(prev);
+  delete s;
+  return VRT_OK;
+}
+
+}  // extern "C"

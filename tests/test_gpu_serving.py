@@ -1,0 +1,145 @@
+"""The serving loop (continuous batching of frame requests over resident line
+sets): every served frame equals, bitwise, the same frame rendered alone
+through the plain calls on a grid that saw the same updates in the same order,
+with several frames on the device at once and with sets evicted and uploaded
+again under a small HBM budget."""
+import numpy as np
+import pytest
+
+import paper_2510_09081_gb300 as vrt
+from gen.linesets import Camera, tiny_walks
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _sets():
+    return [tiny_walks(n_lines=400, n_verts=40, n=64, seed=31),
+            tiny_walks(n_lines=1500, n_verts=60, n=64, radius=0.3, seed=32),
+            tiny_walks(n_lines=300, n_verts=30, n=32, radius=0.5, seed=33, start_lo=4.0, start_hi=28.0),
+            tiny_walks(n_lines=2500, n_verts=50, n=64, seed=34)]
+
+
+def _camera(rng, n, w, h):
+    th = rng.uniform(0, 2 * np.pi)
+    eye = (n / 2 + 1.6 * n * np.cos(th), n / 2 + 1.6 * n * np.sin(th), n / 2 + 0.4 * n)
+    return Camera(width=w, height=h, ortho=0, eye=tuple(map(float, eye)),
+                  target=(n / 2, n / 2, n / 2), up=(0, 0, 1), fovy_deg=45.0)
+
+
+def _requests(sets, n_req, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n_req):
+        k = int(rng.integers(len(sets)))
+        ls = sets[k]
+        w, h = int(rng.integers(40, 97)), int(rng.integers(30, 71))
+        upd = None
+        first = 0
+        if rng.uniform() < 0.6:  # move a block of vertices a little
+            cnt = int(rng.integers(1, ls.n_vertices // 10))
+            first = int(rng.integers(0, ls.n_vertices - cnt))
+            upd = np.clip(ls.xyz[first:first + cnt] + rng.normal(0, 0.2, (cnt, 3)), 1.0,
+                          ls.n - 1.0).astype(np.float32)
+        reqs.append(dict(set=k, cam=_camera(rng, ls.n, w, h), alpha=float(rng.uniform(0.2, 1.0)),
+                         ao=int(rng.uniform() < 0.3) * 6, cull=int(rng.uniform() < 0.5),
+                         first=first, update=upd))
+    return reqs
+
+
+def _plain(sets, reqs):
+    rs = []
+    for ls in sets:
+        r = vrt.Renderer(ls.n, ls.radius)
+        r.upload(ls.xyz, ls.offsets)
+        rs.append(r)
+    out = []
+    for q in reqs:
+        r = rs[q["set"]]
+        if q["update"] is not None:
+            r.update(q["first"], q["update"])
+        rgba, fid, ft = r.frame(q["cam"], alpha=q["alpha"], ao_cones=q["ao"], cull_on=q["cull"])
+        vrt.sync(r.h)
+        out.append((rgba.cpu().numpy().copy(), fid.cpu().numpy().copy(), ft.cpu().numpy().copy()))
+    for r in rs:
+        r.close()
+    return out
+
+
+def _served(sets, reqs, **kw):
+    srv = vrt.Server(**kw)
+    ids = [srv.add_set(ls.xyz, ls.offsets, ls.n, ls.radius) for ls in sets]
+    bufs, rid = [], {}
+    for i, q in enumerate(reqs):
+        c = q["cam"]
+        b = (torch.zeros((c.height, c.width, 4), device="cuda"),
+             torch.zeros((c.height, c.width), dtype=torch.int32, device="cuda"),
+             torch.zeros((c.height, c.width), device="cuda"))
+        bufs.append(b)
+        rid[srv.submit(ids[q["set"]], c, b[0], alpha=q["alpha"], ao_cones=q["ao"], cull_on=q["cull"],
+                       first_id=b[1], first_t=b[2], first_vertex=q["first"], update=q["update"])] = i
+    res = srv.poll(wait=True)
+    stats = srv.stats()
+    srv.close()
+    torch.cuda.synchronize()
+    assert len(res) == len(reqs)
+    for x in res:
+        assert x["status"] == 0, x
+        assert x["latency_ms"] >= x["queue_ms"] >= 0.0
+    out = [(b[0].cpu().numpy(), b[1].cpu().numpy(), b[2].cpu().numpy()) for b in bufs]
+    return out, res, stats
+
+
+def _assert_equal(a, b):
+    for i, (x, y) in enumerate(zip(a, b)):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v), i
+
+
+def test_served_frames_equal_frames_alone():
+    sets = _sets()
+    reqs = _requests(sets, 40, seed=5)
+    alone = _plain(sets, reqs)
+    served, res, stats = _served(sets, reqs, max_inflight=4)
+    _assert_equal(served, alone)
+    assert stats["completed"] == len(reqs) and stats["evictions"] == 0
+    assert stats["resident_sets"] == len(sets)
+
+
+def test_served_frames_with_evictions_equal_frames_alone():
+    sets = _sets()
+    reqs = _requests(sets, 40, seed=6)
+    alone = _plain(sets, reqs)
+    # measure the sets' footprints, then allow about two of them at a time
+    sizes = []
+    for ls in sets:
+        r = vrt.Renderer(ls.n, ls.radius)
+        r.upload(ls.xyz, ls.offsets)
+        r.frame(_camera(np.random.default_rng(0), ls.n, 96, 70), alpha=0.5, ao_cones=6, cull_on=1)
+        vrt.sync(r.h)
+        sizes.append(vrt.grid_device_bytes(r.h))
+        r.close()
+    budget = int(sorted(sizes)[-1] + sorted(sizes)[-2] * 1.05)
+    served, res, stats = _served(sets, reqs, max_inflight=3, hbm_budget=budget)
+    _assert_equal(served, alone)
+    assert stats["evictions"] > 0
+    assert stats["resident_bytes"] <= budget
+
+
+def test_server_errors():
+    sets = _sets()[:1]
+    srv = vrt.Server(max_inflight=2, hbm_budget=1 << 20)  # too small for any set
+    sid = srv.add_set(sets[0].xyz, sets[0].offsets, sets[0].n, sets[0].radius)
+    cam = _camera(np.random.default_rng(1), 64, 32, 24)
+    rgba = torch.zeros((24, 32, 4), device="cuda")
+    with pytest.raises(vrt.VrtError) as e:
+        srv.submit(sid + 5, cam, rgba)
+    assert e.value.status == vrt.ERR_INVALID_ARG
+    with pytest.raises(vrt.VrtError) as e:
+        srv.submit(sid, cam, rgba, first_vertex=sets[0].n_vertices, update=np.zeros((4, 3), np.float32))
+    assert e.value.status == vrt.ERR_INVALID_ARG
+    srv.submit(sid, cam, rgba)
+    res = srv.poll(wait=True)
+    assert len(res) == 1 and res[0]["status"] == vrt.ERR_OOM
+    srv.close()
