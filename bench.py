@@ -405,6 +405,91 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+# ------------------------------------------------------------ serving (C4)
+SERVE_METRIC = "served frames/s over 64 resident line sets (Poisson 200 req/s); p50/p99 latency"
+
+
+def run_serve(args, rank):
+    """Frame requests over 64 resident random-walk line sets of log-uniform size
+    (10k..5M segments; grid 128^3 / 256^3 / 512^3 by size), each request a camera
+    (720p..4K), an opacity in [0.2, 1] and an update of 2% of the set's vertices.
+    Two loads: a Poisson stream at 200 requests/s (latency) and every request
+    queued at once (capacity); each with 4 stream slots (served) and with 1 (the
+    plain one-frame-at-a-time path)."""
+    if rank != 0:
+        return None
+    import torch
+    import paper_2510_09081_gb300 as vrt
+    from gen import linesets as G
+    rng = np.random.default_rng(20251013)
+    n_sets = 64
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(5e6), n_sets)).astype(np.int64)
+    t0 = time.time()
+    sets = []
+    for k, S in enumerate(sizes):
+        n = 128 if S < 200_000 else (256 if S < 1_500_000 else 512)
+        sets.append(G.walk_set(int(S), n, radius=0.4, seed=20251100 + 7 * k))
+    log(f"[bench] {n_sets} sets, {int(sizes.sum())} segments, ready in {time.time() - t0:.1f}s")
+    res_choices = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
+    n_req = max(args.steps, 40)
+    arrivals = np.cumsum(rng.exponential(1.0 / 200.0, n_req))
+    reqs = []
+    for i in range(n_req):
+        k = int(rng.integers(n_sets))
+        ls = sets[k]
+        w, h = res_choices[int(rng.integers(len(res_choices)))]
+        th = rng.uniform(0, 2 * np.pi)
+        c = ls.n / 2.0
+        cam = G.Camera(width=w, height=h, ortho=0,
+                       eye=(c + 1.7 * ls.n * np.cos(th), c + 1.7 * ls.n * np.sin(th), c + 0.5 * ls.n),
+                       target=(c, c, c), up=(0.0, 0.0, 1.0), fovy_deg=45.0)
+        cnt = max(1, ls.n_vertices // 50)
+        first = int(rng.integers(0, ls.n_vertices - cnt + 1))
+        upd = np.clip(ls.xyz[first:first + cnt] + rng.normal(0, 0.05, (cnt, 3)), 1.0,
+                      ls.n - 1.0).astype(np.float32)
+        reqs.append((k, cam, float(rng.uniform(0.2, 1.0)), first, upd))
+    dev = torch.device("cuda", 0)
+    bufs = [torch.empty((2160, 3840, 4), dtype=torch.float32, device=dev) for _ in range(n_sets)]
+
+    def arm(slots, paced):
+        srv = vrt.Server(max_inflight=slots)
+        ids = [srv.add_set(ls.xyz, ls.offsets, ls.n, ls.radius) for ls in sets]
+        # warm-up (not timed): one frame of every set makes it resident
+        for k in range(n_sets):
+            srv.submit(ids[k], reqs[0][1], bufs[k], alpha=0.5)
+        srv.poll(wait=True)
+        t_start = time.perf_counter()
+        for i, (k, cam, alpha, first, upd) in enumerate(reqs):
+            if paced:
+                delay = t_start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            srv.submit(ids[k], cam, bufs[k], alpha=alpha, cull_on=1, first_vertex=first, update=upd)
+        res = srv.poll(wait=True)
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["latency_ms"] for r in res])
+        bad = sum(r["status"] != 0 for r in res)
+        return dict(frames_per_s=round(len(res) / wall, 2), p50_ms=round(float(np.percentile(lat, 50)), 3),
+                    p99_ms=round(float(np.percentile(lat, 99)), 3), failed=int(bad),
+                    resident_sets=st["resident_sets"], evictions=st["evictions"])
+
+    out = {"served_poisson": arm(4, True), "plain_poisson": arm(1, True),
+           "served_capacity": arm(4, False), "plain_capacity": arm(1, False)}
+    sp = out["served_capacity"]["frames_per_s"]
+    return {"metric": SERVE_METRIC, "value": sp, "unit": "frames/s", "n_gpus": 1, "steps": n_req,
+            "warmup": n_sets, "ms_per_step": round(1000.0 / sp, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "ours",
+            "config": {"workload": ("serving: 64 resident random-walk line sets, log-uniform "
+                                    "10k..5M segments (total %d), grids 128^3..512^3, outputs "
+                                    "720p..4K, alpha U[0.2, 1], 2%% of vertices updated per "
+                                    "request, culling on" % int(sizes.sum())),
+                       "value_definition": "frames/s with every request queued at once, 4 stream slots",
+                       **out}}
+
+
 # ----------------------------------------------------------- reference arm
 def run_reference(args, rank):
     """The oracle, as it stands, on the host cores; each step is a bounded
@@ -435,7 +520,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc"])
+    ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mips", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="storage of the occupancy pyramid (AO workloads)")
@@ -452,6 +537,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         out = run_reference(args, rank)
+    elif args.workload == "serve":
+        out = run_serve(args, rank)
     else:
         out = run_ours(args, rank, world, local_rank)
     if out is not None:

@@ -112,6 +112,30 @@ def tiny_walks(n_lines=2000, n_verts=50, n=64, radius=0.4, step=0.5,
     return LineSet(xyz=xyz, offsets=offsets, n=n, radius=radius)
 
 
+def walk_set(n_segments, n, radius=0.4, verts_range=(20, 200), seed=SEED_BASE + 3,
+             step=0.5, turn_deg=10.0) -> LineSet:
+    """Random walks (as tiny_walks) of uniformly random length in verts_range,
+    about n_segments segments in all, starting anywhere in the grid's interior."""
+    rng = np.random.default_rng(seed)
+    lo, hi = verts_range
+    lens = []
+    segs = 0
+    while segs < n_segments:
+        L = int(rng.integers(lo, hi + 1))
+        L = min(L, n_segments - segs + 1)
+        if L < 2:
+            break
+        lens.append(L)
+        segs += L - 1
+    lens = np.asarray(lens, dtype=np.int64)
+    full = tiny_walks(n_lines=lens.shape[0], n_verts=int(lens.max()), n=n, radius=radius, step=step,
+                      turn_deg=turn_deg, seed=seed + 1, start_lo=2.0, start_hi=float(n - 2))
+    keep = np.arange(int(lens.max()))[None, :] < lens[:, None]
+    xyz = full.xyz.reshape(lens.shape[0], int(lens.max()), 3)[keep]
+    offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    return LineSet(xyz=np.ascontiguousarray(xyz, np.float32), offsets=offsets, n=n, radius=radius)
+
+
 def tiny_walks_camera(n=64, width=256, height=256) -> Camera:
     c = n / 2.0
     return Camera(width=width, height=height, ortho=1,

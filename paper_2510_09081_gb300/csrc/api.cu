@@ -34,6 +34,7 @@ struct vrt_grid_s {
   uint8_t *bdist = nullptr, *btmp = nullptr;  // empty-brick distance field and its scratch
   uint32_t* need = nullptr;
   uint8_t* eroded = nullptr;
+  uint8_t* cdist = nullptr;  // [bricks] distance to a brick with eroded occupancy
   uint32_t* lists = nullptr;
   unsigned long long list_cap = 0;
   uint2* xq = nullptr;      // pairs the fp32 filter left to the exact path
@@ -285,7 +286,7 @@ void free_all(vrt_grid g) {
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
   dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm);
   dfree(g, g->word); dfree(g, g->cur); dfree(g, g->vis); dfree(g, g->bdist); dfree(g, g->btmp);
-  dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->lists); dfree(g, g->tile_state);
+  dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->cdist); dfree(g, g->lists); dfree(g, g->tile_state);
   dfree(g, g->xq); dfree(g, g->rec);
   dfree(g, g->mips); dfree(g, g->vq[0]); dfree(g, g->vq[1]); dfree(g, g->pq[0]); dfree(g, g->pq[1]);
   dfree(g, g->resume);
@@ -513,7 +514,8 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   stage_mark(g, ST_CULL, 0);
   if (p->cull) {
     if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
-    g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->stream);
+    if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
+    g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->btmp, g->cdist, g->stream);
   } else {
     VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
   }

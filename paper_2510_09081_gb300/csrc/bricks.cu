@@ -46,15 +46,21 @@ __global__ void __launch_bounds__(256) k_brick_dist(int log2nb, int axis,
   out[b] = (uint8_t)d;
 }
 
+int launch_brick_dist_passes(int log2nb, uint8_t* tmp, uint8_t* dist, cudaStream_t s) {
+  const uint32_t nb = 1u << (3 * log2nb);
+  const int T = 256;
+  const unsigned blocks = (nb + T - 1) / T;
+  k_brick_dist<<<blocks, T, 0, s>>>(log2nb, 0, tmp, dist);
+  k_brick_dist<<<blocks, T, 0, s>>>(log2nb, 1, dist, tmp);
+  k_brick_dist<<<blocks, T, 0, s>>>(log2nb, 2, tmp, dist);
+  return 3;
+}
+
 int launch_brick_dist(const GridDev& g, uint8_t* tmp, uint8_t* dist, cudaStream_t s) {
   const uint32_t nb = 1u << (3 * g.log2nb);
   const int T = 256;
-  const unsigned blocks = (nb + T - 1) / T;
-  k_brick_occ<<<blocks, T, 0, s>>>(g, tmp);
-  k_brick_dist<<<blocks, T, 0, s>>>(g.log2nb, 0, tmp, dist);
-  k_brick_dist<<<blocks, T, 0, s>>>(g.log2nb, 1, dist, tmp);
-  k_brick_dist<<<blocks, T, 0, s>>>(g.log2nb, 2, tmp, dist);
-  return 4;
+  k_brick_occ<<<(nb + T - 1) / T, T, 0, s>>>(g, tmp);
+  return 1 + launch_brick_dist_passes(g.log2nb, tmp, dist, s);
 }
 
 }  // namespace vrt

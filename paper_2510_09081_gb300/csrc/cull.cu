@@ -12,8 +12,9 @@
 // occupancy estimate's excess over the true tube volume (about 4/3 for thin
 // tubes under the PWAA clamp). A voxel is marked visible unless
 // the depth in front of it exceeds ln(1e4) + 3, past the depth where a ray
-// stops. The march crosses cubes of empty bricks in one step, using the
-// distance field built after pass 1. The marks decide which voxels get lists; voxels a ray later needs but
+// stops. The march crosses, in one step, cubes of bricks without eroded
+// occupancy (they add no depth), using a distance field over such bricks built
+// after the erosion. The marks decide which voxels get lists; voxels a ray later needs but
 // that were left unmarked are listed by the trace's repair rounds, so the
 // marks only affect speed.
 #include <cmath>
@@ -31,21 +32,33 @@ __device__ __forceinline__ uint32_t occ8(const GridDev& g, int x, int y, int z) 
   return min(255u, (uint32_t)((float)q * (255.0f / g.occ_scale)));
 }
 
-__global__ void __launch_bounds__(256) k_erode(GridDev g, uint8_t* __restrict__ eroded) {
+// Erosion, and per brick whether any voxel keeps eroded occupancy (0) or none
+// does (kBrickDistMax), the seed of the march's skipping field. A block covers
+// 4 bricks of 64 consecutive voxels.
+__global__ void __launch_bounds__(256) k_erode(GridDev g, uint8_t* __restrict__ eroded,
+                                               uint8_t* __restrict__ ebrick) {
+  __shared__ uint32_t s_any[4];
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (uint32_t)g.n * g.n * g.n) return;
-  int x, y, z;
-  brick_coords(idx, g.log2nb, x, y, z);
-  uint32_t e = occ8(g, x, y, z);
-  if (e) {
-    e = min(e, occ8(g, x - 1, y, z));
-    e = min(e, occ8(g, x + 1, y, z));
-    e = min(e, occ8(g, x, y - 1, z));
-    e = min(e, occ8(g, x, y + 1, z));
-    e = min(e, occ8(g, x, y, z - 1));
-    e = min(e, occ8(g, x, y, z + 1));
+  if (threadIdx.x < 4) s_any[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t e = 0;
+  if (idx < (uint32_t)g.n * g.n * g.n) {
+    int x, y, z;
+    brick_coords(idx, g.log2nb, x, y, z);
+    e = occ8(g, x, y, z);
+    if (e) {
+      e = min(e, occ8(g, x - 1, y, z));
+      e = min(e, occ8(g, x + 1, y, z));
+      e = min(e, occ8(g, x, y - 1, z));
+      e = min(e, occ8(g, x, y + 1, z));
+      e = min(e, occ8(g, x, y, z - 1));
+      e = min(e, occ8(g, x, y, z + 1));
+    }
+    eroded[idx] = (uint8_t)e;
   }
-  eroded[idx] = (uint8_t)e;
+  if (__any_sync(0xffffffffu, e != 0) && (threadIdx.x & 31) == 0) atomicOr(&s_any[threadIdx.x >> 6], 1u);
+  __syncthreads();
+  if (threadIdx.x < 4) ebrick[blockIdx.x * 4 + threadIdx.x] = s_any[threadIdx.x] ? 0 : (uint8_t)kBrickDistMax;
 }
 
 struct CullCam {
@@ -57,7 +70,8 @@ struct CullCam {
 };
 
 __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
-                                                 const uint8_t* __restrict__ eroded) {
+                                                 const uint8_t* __restrict__ eroded,
+                                                 const uint8_t* __restrict__ cdist) {
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
   bool visible = false;
@@ -84,8 +98,8 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
     }
     if (inside) {
       // march from the centre toward the camera, voxel by voxel through
-      // bricks with occupied voxels and across cubes of empty bricks (which
-      // add no depth) in one step
+      // bricks with eroded occupancy and across cubes of bricks without any
+      // (which add no depth) in one step
       const int n = g.n;
       int px = x, py = y, pz = z;
       const int sx = dir.x > 0.0f ? 1 : (dir.x < 0.0f ? -1 : 0);
@@ -120,7 +134,7 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
         for (int sk = 0; sk < 3 * n; ++sk) {
           const uint32_t bidx = ((uint32_t)(pz >> 2) << (2 * g.log2nb)) |
                                 ((uint32_t)(py >> 2) << g.log2nb) | (uint32_t)(px >> 2);
-          const int kd = __ldg(&g.bdist[bidx]);
+          const int kd = __ldg(&cdist[bidx]);
           if (kd == 0) break;
           const int ext = 4 * (kd - 1), w = 4 + 2 * ext;
           const int bx = (px & ~3) - ext, by = (py & ~3) - ext, bz = (pz & ~3) - ext;
@@ -161,7 +175,7 @@ float3 tof(D3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 }  // namespace
 
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                cudaStream_t s) {
+                uint8_t* btmp, uint8_t* cdist, cudaStream_t s) {
   const D3 eye = {cam.eye[0], cam.eye[1], cam.eye[2]};
   const D3 tgt = {cam.target[0], cam.target[1], cam.target[2]};
   const D3 upw = {cam.up[0], cam.up[1], cam.up[2]};
@@ -191,9 +205,10 @@ int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* e
   cc.lt = (float)(len(nt) * h + 1e-3); cc.lb = (float)(len(nb) * h + 1e-3);
   const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
   const int T = 256;
-  k_erode<<<(nvox + T - 1) / T, T, 0, s>>>(g, eroded);
-  k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded);
-  return 2;
+  k_erode<<<(nvox + T - 1) / T, T, 0, s>>>(g, eroded, btmp);
+  const int passes = launch_brick_dist_passes(g.log2nb, btmp, cdist, s);
+  k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded, cdist);
+  return 2 + passes;
 }
 
 }  // namespace vrt

@@ -58,6 +58,9 @@ int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDe
                   cudaStream_t s);
 // Empty-brick distance field from the counts of pass 1 (tmp: one byte per brick).
 int launch_brick_dist(const GridDev& g, uint8_t* tmp, uint8_t* dist, cudaStream_t s);
+// The three distance passes from per-brick bytes in tmp (0 = occupied, else
+// kBrickDistMax); tmp is overwritten.
+int launch_brick_dist_passes(int log2nb, uint8_t* tmp, uint8_t* dist, cudaStream_t s);
 // Pass 2 over the fragment records. mode 0: every occupied voxel has a list;
 // 1: voxels marked by the cull; 2: repair, only voxels whose `need` bit is set
 // (skipped when *pending is 0).
@@ -68,8 +71,10 @@ int launch_scan(const GridDev& g, int all_visible, unsigned long long* tile_stat
 int launch_finalize(const GridDev& g, cudaStream_t s);
 int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off, int n_levels,
                 cudaStream_t s);
+// Cull marks; btmp, cdist: one byte per brick (scratch; distance to a brick
+// with eroded occupancy).
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                cudaStream_t s);
+                uint8_t* btmp, uint8_t* cdist, cudaStream_t s);
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
 // Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
 // them, then clear their `need` bits and the next round's queue counters.
