@@ -35,6 +35,7 @@ struct vrt_grid_s {
   uint32_t* need = nullptr;
   uint8_t* eroded = nullptr;
   uint8_t* cdist = nullptr;  // [bricks] distance to a brick with eroded occupancy
+  float* emean = nullptr;    // [bricks] mean eroded occupancy
   uint32_t* lists = nullptr;
   unsigned long long list_cap = 0;
   uint2* xq = nullptr;      // pairs the fp32 filter left to the exact path
@@ -286,7 +287,7 @@ void free_all(vrt_grid g) {
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
   dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm);
   dfree(g, g->word); dfree(g, g->cur); dfree(g, g->vis); dfree(g, g->bdist); dfree(g, g->btmp);
-  dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->cdist); dfree(g, g->lists); dfree(g, g->tile_state);
+  dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->cdist); dfree(g, g->emean); dfree(g, g->lists); dfree(g, g->tile_state);
   dfree(g, g->xq); dfree(g, g->rec);
   dfree(g, g->mips); dfree(g, g->vq[0]); dfree(g, g->vq[1]); dfree(g, g->pq[0]); dfree(g, g->pq[1]);
   dfree(g, g->resume);
@@ -515,7 +516,9 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   if (p->cull) {
     if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
     if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
-    g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->btmp, g->cdist, g->stream);
+    if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
+    g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->btmp, g->cdist, g->emean,
+                               g->stream);
   } else {
     VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
   }

@@ -12,9 +12,10 @@
 // occupancy estimate's excess over the true tube volume (about 4/3 for thin
 // tubes under the PWAA clamp). A voxel is marked visible unless
 // the depth in front of it exceeds ln(1e4) + 3, past the depth where a ray
-// stops. The march crosses, in one step, cubes of bricks without eroded
-// occupancy (they add no depth), using a distance field over such bricks built
-// after the erosion. The marks decide which voxels get lists; voxels a ray later needs but
+// stops. The march uses the eroded occupancy at two levels of its pyramid:
+// voxels for the first few voxel lengths, then 4^3 bricks (their mean); it
+// crosses, in one step, cubes of bricks without eroded occupancy (they add no
+// depth), using a distance field over such bricks built after the erosion. The marks decide which voxels get lists; voxels a ray later needs but
 // that were left unmarked are listed by the trace's repair rounds, so the
 // marks only affect speed.
 #include <cmath>
@@ -36,10 +37,11 @@ __device__ __forceinline__ uint32_t occ8(const GridDev& g, int x, int y, int z) 
 // does (kBrickDistMax), the seed of the march's skipping field. A block covers
 // 4 bricks of 64 consecutive voxels.
 __global__ void __launch_bounds__(256) k_erode(GridDev g, uint8_t* __restrict__ eroded,
-                                               uint8_t* __restrict__ ebrick) {
-  __shared__ uint32_t s_any[4];
+                                               uint8_t* __restrict__ ebrick,
+                                               float* __restrict__ emean) {
+  __shared__ uint32_t s_any[4], s_sum[4];
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (threadIdx.x < 4) s_any[threadIdx.x] = 0;
+  if (threadIdx.x < 4) s_any[threadIdx.x] = s_sum[threadIdx.x] = 0;
   __syncthreads();
   uint32_t e = 0;
   if (idx < (uint32_t)g.n * g.n * g.n) {
@@ -56,9 +58,18 @@ __global__ void __launch_bounds__(256) k_erode(GridDev g, uint8_t* __restrict__ 
     }
     eroded[idx] = (uint8_t)e;
   }
-  if (__any_sync(0xffffffffu, e != 0) && (threadIdx.x & 31) == 0) atomicOr(&s_any[threadIdx.x >> 6], 1u);
+  uint32_t esum = e;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+  if ((threadIdx.x & 31) == 0 && esum) {
+    atomicOr(&s_any[threadIdx.x >> 6], 1u);
+    atomicAdd(&s_sum[threadIdx.x >> 6], esum);
+  }
   __syncthreads();
-  if (threadIdx.x < 4) ebrick[blockIdx.x * 4 + threadIdx.x] = s_any[threadIdx.x] ? 0 : (uint8_t)kBrickDistMax;
+  if (threadIdx.x < 4) {
+    ebrick[blockIdx.x * 4 + threadIdx.x] = s_any[threadIdx.x] ? 0 : (uint8_t)kBrickDistMax;
+    emean[blockIdx.x * 4 + threadIdx.x] = (float)s_sum[threadIdx.x] * (1.0f / (255.0f * 64.0f));
+  }
 }
 
 struct CullCam {
@@ -69,9 +80,13 @@ struct CullCam {
   int ortho;
 };
 
+// Voxel steps of the march before it continues brick by brick.
+constexpr float kCullNear = 6.0f;
+
 __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
                                                  const uint8_t* __restrict__ eroded,
-                                                 const uint8_t* __restrict__ cdist) {
+                                                 const uint8_t* __restrict__ cdist,
+                                                 const float* __restrict__ emean) {
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
   bool visible = false;
@@ -97,10 +112,11 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
       tmax = dist;
     }
     if (inside) {
-      // march from the centre toward the camera, voxel by voxel through
-      // bricks with eroded occupancy and across cubes of bricks without any
-      // (which add no depth) in one step
-      const int n = g.n;
+      // March from the centre toward the camera through the eroded occupancy
+      // pyramid: voxel by voxel for the first kCullNear voxel lengths, then
+      // brick by brick with each 4^3 brick's mean, crossing cubes of bricks
+      // without eroded occupancy (which add no depth) in one step.
+      const int n = g.n, nb = n >> 2;
       int px = x, py = y, pz = z;
       const int sx = dir.x > 0.0f ? 1 : (dir.x < 0.0f ? -1 : 0);
       const int sy = dir.y > 0.0f ? 1 : (dir.y < 0.0f ? -1 : 0);
@@ -114,8 +130,10 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
       };
       float depth = 0.0f, tcur = 0.0f;
       bool counted = false;  // the voxel itself adds nothing to the depth in front of it
+      bool done = false;
       visible = true;
-      for (int it = 0; it < 3 * n + 16; ++it) {
+      // near: voxels
+      for (int it = 0; it < 3 * n + 16 && !done; ++it) {
         const float tx = leave(sx, px, px + 1, c.x, ix);
         const float ty = leave(sy, py, py + 1, c.y, iy);
         const float tz = leave(sz, pz, pz + 1, c.z, iz);
@@ -123,39 +141,52 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
         if (counted) {
           const float e = (float)__ldg(&eroded[brick_index(px, py, pz, g.log2nb)]) * (1.0f / 255.0f);
           depth = fmaf(cc.kappa * e, fminf(te, tmax) - tcur, depth);
-          if (depth > kCullDepth) { visible = false; break; }
+          if (depth > kCullDepth) { visible = false; done = true; break; }
         }
         counted = true;
-        if (te >= tmax) break;
+        if (te >= tmax) { done = true; break; }
         if (te == tx) px += sx; else if (te == ty) py += sy; else pz += sz;
-        if ((unsigned)px >= (unsigned)n || (unsigned)py >= (unsigned)n || (unsigned)pz >= (unsigned)n) break;
-        tcur = te;
-        bool done = false;
-        for (int sk = 0; sk < 3 * n; ++sk) {
-          const uint32_t bidx = ((uint32_t)(pz >> 2) << (2 * g.log2nb)) |
-                                ((uint32_t)(py >> 2) << g.log2nb) | (uint32_t)(px >> 2);
-          const int kd = __ldg(&cdist[bidx]);
-          if (kd == 0) break;
-          const int ext = 4 * (kd - 1), w = 4 + 2 * ext;
-          const int bx = (px & ~3) - ext, by = (py & ~3) - ext, bz = (pz & ~3) - ext;
-          const float ux = leave(sx, bx, bx + w, c.x, ix);
-          const float uy = leave(sy, by, by + w, c.y, iy);
-          const float uz = leave(sz, bz, bz + w, c.z, iz);
-          const float tb = fminf(ux, fminf(uy, uz));
-          if (tb >= tmax) { done = true; break; }
-          const int qx = min(min(bx + w, n) - 1, max(max(bx, 0), (int)floorf(fmaf(tb, dir.x, c.x))));
-          const int qy = min(min(by + w, n) - 1, max(max(by, 0), (int)floorf(fmaf(tb, dir.y, c.y))));
-          const int qz = min(min(bz + w, n) - 1, max(max(bz, 0), (int)floorf(fmaf(tb, dir.z, c.z))));
-          if (tb == ux) { px = sx > 0 ? bx + w : bx - 1; py = qy; pz = qz; }
-          else if (tb == uy) { py = sy > 0 ? by + w : by - 1; px = qx; pz = qz; }
-          else { pz = sz > 0 ? bz + w : bz - 1; px = qx; py = qy; }
-          if ((unsigned)px >= (unsigned)n || (unsigned)py >= (unsigned)n || (unsigned)pz >= (unsigned)n) {
-            done = true;
-            break;
-          }
-          tcur = tb;
+        if ((unsigned)px >= (unsigned)n || (unsigned)py >= (unsigned)n || (unsigned)pz >= (unsigned)n) {
+          done = true;
+          break;
         }
-        if (done) break;
+        tcur = te;
+        if (tcur >= kCullNear) break;  // on to bricks, at voxel p from tcur
+      }
+      // far: bricks (brick coordinates bx, by, bz; the march is in brick b from tcur)
+      int bx = px >> 2, by = py >> 2, bz = pz >> 2;
+      for (int it = 0; it < 3 * nb + 16 && !done; ++it) {
+        const uint32_t bidx = ((uint32_t)bz << (2 * g.log2nb)) | ((uint32_t)by << g.log2nb) | (uint32_t)bx;
+        const int kd = __ldg(&cdist[bidx]);
+        if (kd > 0) {
+          // cross the cube of bricks within kd - 1 of this one (voxel box [lo, lo + w))
+          const int ext = kd - 1;
+          const int lx = 4 * (bx - ext), ly = 4 * (by - ext), lz = 4 * (bz - ext), w = 4 * (2 * ext + 1);
+          const float ux = leave(sx, lx, lx + w, c.x, ix);
+          const float uy = leave(sy, ly, ly + w, c.y, iy);
+          const float uz = leave(sz, lz, lz + w, c.z, iz);
+          const float tb = fminf(ux, fminf(uy, uz));
+          if (tb >= tmax) break;
+          const int qx = min(min(bx + ext, nb - 1), max(max(bx - ext, 0), (int)floorf(fmaf(tb, dir.x, c.x) * 0.25f)));
+          const int qy = min(min(by + ext, nb - 1), max(max(by - ext, 0), (int)floorf(fmaf(tb, dir.y, c.y) * 0.25f)));
+          const int qz = min(min(bz + ext, nb - 1), max(max(bz - ext, 0), (int)floorf(fmaf(tb, dir.z, c.z) * 0.25f)));
+          if (tb == ux) { bx = sx > 0 ? bx + ext + 1 : bx - ext - 1; by = qy; bz = qz; }
+          else if (tb == uy) { by = sy > 0 ? by + ext + 1 : by - ext - 1; bx = qx; bz = qz; }
+          else { bz = sz > 0 ? bz + ext + 1 : bz - ext - 1; bx = qx; by = qy; }
+          if ((unsigned)bx >= (unsigned)nb || (unsigned)by >= (unsigned)nb || (unsigned)bz >= (unsigned)nb) break;
+          tcur = tb;
+          continue;
+        }
+        const float tx = leave(sx, 4 * bx, 4 * bx + 4, c.x, ix);
+        const float ty = leave(sy, 4 * by, 4 * by + 4, c.y, iy);
+        const float tz = leave(sz, 4 * bz, 4 * bz + 4, c.z, iz);
+        const float te = fminf(tx, fminf(ty, tz));
+        depth = fmaf(cc.kappa * __ldg(&emean[bidx]), fminf(te, tmax) - tcur, depth);
+        if (depth > kCullDepth) { visible = false; break; }
+        if (te >= tmax) break;
+        if (te == tx) bx += sx; else if (te == ty) by += sy; else bz += sz;
+        if ((unsigned)bx >= (unsigned)nb || (unsigned)by >= (unsigned)nb || (unsigned)bz >= (unsigned)nb) break;
+        tcur = te;
       }
     }
   }
@@ -175,7 +206,7 @@ float3 tof(D3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 }  // namespace
 
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                uint8_t* btmp, uint8_t* cdist, cudaStream_t s) {
+                uint8_t* btmp, uint8_t* cdist, float* emean, cudaStream_t s) {
   const D3 eye = {cam.eye[0], cam.eye[1], cam.eye[2]};
   const D3 tgt = {cam.target[0], cam.target[1], cam.target[2]};
   const D3 upw = {cam.up[0], cam.up[1], cam.up[2]};
@@ -205,9 +236,9 @@ int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* e
   cc.lt = (float)(len(nt) * h + 1e-3); cc.lb = (float)(len(nb) * h + 1e-3);
   const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
   const int T = 256;
-  k_erode<<<(nvox + T - 1) / T, T, 0, s>>>(g, eroded, btmp);
+  k_erode<<<(nvox + T - 1) / T, T, 0, s>>>(g, eroded, btmp, emean);
   const int passes = launch_brick_dist_passes(g.log2nb, btmp, cdist, s);
-  k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded, cdist);
+  k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded, cdist, emean);
   return 2 + passes;
 }
 

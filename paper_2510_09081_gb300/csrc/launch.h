@@ -72,9 +72,9 @@ int launch_finalize(const GridDev& g, cudaStream_t s);
 int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off, int n_levels,
                 cudaStream_t s);
 // Cull marks; btmp, cdist: one byte per brick (scratch; distance to a brick
-// with eroded occupancy).
+// with eroded occupancy); emean: one float per brick (mean eroded occupancy).
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                uint8_t* btmp, uint8_t* cdist, cudaStream_t s);
+                uint8_t* btmp, uint8_t* cdist, float* emean, cudaStream_t s);
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
 // Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
 // them, then clear their `need` bits and the next round's queue counters.
