@@ -91,7 +91,12 @@ typedef struct {
   int32_t ao_cones; /* 0: no ambient occlusion; 6: six cones per hit */
   int32_t cull;     /* 0: lists for every voxel (voxelize-scan-voxelize);
                        1: lists for camera-visible voxels only
-                       (voxelize-cull-scan-voxelize) */
+                       (voxelize-cull-scan-voxelize);
+                       2: automatic: as 1, except that the grid skips the
+                       cull (as 0) while the last culled build it has seen
+                       (through vrt_sync or vrt_get_stats) kept more than 95%
+                       of the occupied voxels, culling again every 8th build.
+                       The image is the same in every mode. */
   int32_t k;        /* 0, 1, 8, 16 or 32; kept for compatibility: the trace
                        keeps 4 nearest keys per lane (128 per warp) and
                        rescans a list when it must, so the image does not

@@ -64,6 +64,10 @@ struct vrt_grid_s {
   int stage = 0;  // 0 created, 1 vertices set, 2 voxelized, 3 lists built
   bool mips_valid = false;
   int culled = 0;
+  // automatic culling: visible / occupied voxels of the last culled list build
+  // seen on the host (-1: not yet), and list builds since the last cull
+  double auto_vis_frac = -1.0;
+  int auto_skipped = 0;
   std::string err;
   // device memory held by this grid
   std::unordered_map<void*, size_t> alloc_bytes;
@@ -502,18 +506,27 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
   if (!p) return fail(g, VRT_ERR_INVALID_ARG, "params is NULL");
   if (g->stage < 2) return fail(g, VRT_ERR_STATE, "vrt_voxelize first");
+  if (p->cull < 0 || p->cull > 2) return fail(g, VRT_ERR_INVALID_ARG, "cull must be 0, 1 or 2");
   if (p->cull && !camera_ok(cam)) return fail(g, VRT_ERR_INVALID_ARG, "bad camera");
   if (p->cull && !(p->alpha > 0.0f && p->alpha <= 1.0f))
     return fail(g, VRT_ERR_INVALID_ARG, "alpha must be in (0, 1]");
   const size_t nv = (size_t)g->n * g->n * g->n;
   const GridDev d = gdev(g);
+  // automatic: cull unless the last culled build kept more than 95% of the
+  // occupied voxels (then culling costs more than it saves); look again every
+  // 8 builds
+  int cull = p->cull;
+  if (cull == 2) {
+    cull = g->auto_vis_frac < 0.0 || g->auto_vis_frac <= 0.95 || g->auto_skipped >= 8;
+    g->auto_skipped = cull ? 0 : g->auto_skipped + 1;
+  }
   // reset the list-build counters (scan tile counter .. end)
   const size_t off = offsetof(DevStatus, sum_count_field);
   VRT_CUDA(g, cudaMemsetAsync((char*)g->st + off, 0, sizeof(DevStatus) - off, g->stream));
   VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, occupied_voxels), 0, sizeof(unsigned int), g->stream));
   VRT_CUDA(g, cudaMemsetAsync(g->tile_state, 0, (size_t)g->n_tiles * 8, g->stream));
   stage_mark(g, ST_CULL, 0);
-  if (p->cull) {
+  if (cull) {
     if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
     if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
     if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
@@ -524,14 +537,14 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   }
   stage_mark(g, ST_CULL, 1);
   stage_mark(g, ST_SCAN, 0);
-  g->launches += launch_scan(d, p->cull ? 0 : 1, g->tile_state, g->n_tiles, g->stream);
+  g->launches += launch_scan(d, cull ? 0 : 1, g->tile_state, g->n_tiles, g->stream);
   g->launches += launch_finalize(d, g->stream);
   stage_mark(g, ST_SCAN, 1);
   stage_mark(g, ST_PASS2, 0);
-  g->launches += launch_scatter(d, p->cull ? 1 : 0, nullptr, nullptr, g->stream);
+  g->launches += launch_scatter(d, cull ? 1 : 0, nullptr, nullptr, g->stream);
   stage_mark(g, ST_PASS2, 1);
   VRT_CUDA(g, cudaGetLastError());
-  g->culled = p->cull ? 1 : 0;
+  g->culled = cull ? 1 : 0;
   g->stage = 3;
   return VRT_OK;
 }
@@ -624,11 +637,17 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   return VRT_OK;
 }
 
+// For automatic culling: the visible share of the last culled list build.
+static void note_visibility(vrt_grid g, const DevStatus& hs) {
+  if (g->culled && hs.occupied_voxels) g->auto_vis_frac = (double)hs.visible_voxels / hs.occupied_voxels;
+}
+
 vrt_status vrt_sync(vrt_grid g) {
   if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
   VRT_CUDA(g, cudaStreamSynchronize(g->stream));
   DevStatus hs;
   VRT_CUDA(g, cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost));
+  note_visibility(g, hs);
   uint32_t e = hs.err;
   if (g->culled && hs.vq_cnt[kMaxRepairRounds & 1] != 0) e |= kErrRepair;
   if (hs.err) VRT_CUDA(g, cudaMemset(g->st, 0, sizeof(unsigned int)));
@@ -645,6 +664,7 @@ vrt_status vrt_get_stats(vrt_grid g, vrt_stats* out) {
   VRT_CUDA(g, cudaStreamSynchronize(g->stream));
   DevStatus hs;
   VRT_CUDA(g, cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost));
+  note_visibility(g, hs);
   out->fragments = hs.F;
   out->fragments_listed = hs.listed;
   out->sum_occupancy = hs.sum_q;
@@ -690,6 +710,7 @@ vrt_status vrt_read_lists(vrt_grid g, uint32_t* start, uint32_t* len, uint32_t* 
   VRT_CUDA(g, cudaMemcpy(c.data(), g->cur, nv * 4, cudaMemcpyDeviceToHost));
   VRT_CUDA(g, cudaMemcpy(vis.data(), g->vis, nv / 8, cudaMemcpyDeviceToHost));
   VRT_CUDA(g, cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost));
+  note_visibility(g, hs);
   for (int z = 0; z < n; ++z)
     for (int y = 0; y < n; ++y)
       for (int x = 0; x < n; ++x) {

@@ -195,6 +195,38 @@ def test_culling_never_changes_the_image(alpha):
     assert st["visible_voxels"] < st["occupied_voxels"]
 
 
+def test_automatic_culling():
+    # cull = 2: the image is that of cull = 0 in every frame; a set the cull
+    # keeps almost entirely stops being culled after its first culled frame
+    ls = tiny_walks(n_lines=3000, n_verts=60, seed=9)
+    cam = _persp_cam(w=211, h=117)
+    r = gpu_grid(ls)
+    off = gpu_image(r, cam, alpha=0.3, cull=0)
+    vis = []
+    for f in range(4):
+        img = gpu_image(r, cam, alpha=0.3, cull=2)
+        st = vrt.get_stats(r.h)
+        vis.append((st["visible_voxels"], st["occupied_voxels"]))
+        for a, b in zip(off, img):
+            assert np.array_equal(a, b)
+    r.close()
+    frac = vis[0][0] / vis[0][1]
+    if frac > 0.95:   # kept almost everything: later builds skip the cull
+        assert all(v == o for v, o in vis[1:])
+    else:             # culling pays: every build culls
+        assert all(v < o for v, o in vis)
+    # a sparse set in front of the camera keeps everything visible
+    sp = tiny_walks(n_lines=40, n_verts=30, seed=10)
+    r = gpu_grid(sp)
+    gpu_image(r, cam, alpha=0.3, cull=2)
+    st0 = vrt.get_stats(r.h)
+    gpu_image(r, cam, alpha=0.3, cull=2)
+    st1 = vrt.get_stats(r.h)
+    r.close()
+    assert st0["visible_voxels"] / st0["occupied_voxels"] > 0.95
+    assert st1["visible_voxels"] == st1["occupied_voxels"]
+
+
 def test_mips_match_oracle():
     ls = tiny_walks(n_lines=800, n_verts=50, n=64, seed=3)
     o = oracle.Oracle.from_lineset(ls)
