@@ -35,10 +35,14 @@ constexpr unsigned FULLW = 0xffffffffu;
 struct Walk {
   float3 a, b;
   float am, a1, a2, s1, s2, rho1, rho2, lo_m, hi_m;
-  float inv_w12, inv_w2;  // reciprocals of W1 * W2 and W2 for the decode
+  float inv_w12, inv_w2;  // reciprocals of W1 * W2 and W2 for the uniform decode
   int m, c0, W1, W2;
-  uint32_t n;  // candidates: slabs * W1 * W2
+  bool exact;             // candidates are exactly the slab boxes' voxels
+  uint32_t pre[4];        // exact: 16-bit cumulative counts after slabs 0..7
+  uint32_t n;             // candidates
 };
+
+constexpr int kExactSlabs = 9;  // slabs whose boxes the exact decode indexes
 
 // Minor-axis voxel ranges of slab c (clamped to the grid): the axis line
 // a_k + (x - a_m) s_k over the slab's part of [lo_m, hi_m], widened by rho_k.
@@ -76,28 +80,50 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
   w.a2 = cmp3(a, k2);
   w.c0 = max(0, (int)floorf(w.lo_m - kWalkEps));
   const int c1 = min(n - 1, (int)floorf(w.hi_m + kWalkEps));
-  // index every slab's box with the widest slab's widths
+  // Up to kExactSlabs slabs: candidates are the voxels of each slab's own box,
+  // numbered slab after slab (cumulative counts kept); longer segments index
+  // every slab's box with the widest slab's widths.
   int W1 = 1, W2 = 1;
-  for (int c = w.c0; c <= c1; ++c) {
+  uint32_t total = 0;
+  w.pre[0] = w.pre[1] = w.pre[2] = w.pre[3] = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < kExactSlabs; ++k) {  // unrolled: pre[] stays in registers
+    const int c = w.c0 + k;
+    if (c > c1) break;
+    int j0, j1, l0, l1;
+    slab_box(w.am, w.a1, w.a2, w.s1, w.s2, w.rho1, w.rho2, w.lo_m, w.hi_m, n, c, j0, j1, l0, l1);
+    W1 = max(W1, j1 - j0 + 1);
+    W2 = max(W2, l1 - l0 + 1);
+    total += (uint32_t)(max(0, j1 - j0 + 1) * max(0, l1 - l0 + 1));
+    if (k < 8) {  // cumulative count after slab k
+      const uint32_t v = min(total, 0xffffu);
+      w.pre[k >> 1] = (w.pre[k >> 1] & ~(0xffffu << (16 * (k & 1)))) | (v << (16 * (k & 1)));
+    }
+  }
+  for (int c = w.c0 + kExactSlabs; c <= c1; ++c) {  // longer segments: widths only
     int j0, j1, l0, l1;
     slab_box(w.am, w.a1, w.a2, w.s1, w.s2, w.rho1, w.rho2, w.lo_m, w.hi_m, n, c, j0, j1, l0, l1);
     W1 = max(W1, j1 - j0 + 1);
     W2 = max(W2, l1 - l0 + 1);
   }
+  const int slabs = c1 - w.c0 + 1;
   w.W1 = W1;
   w.W2 = W2;
-  w.n = c1 >= w.c0 ? (uint32_t)(c1 - w.c0 + 1) * (uint32_t)(w.W1 * w.W2) : 0u;
-  w.inv_w12 = 1.0f / (float)(w.W1 * w.W2);
-  w.inv_w2 = 1.0f / (float)w.W2;
+  w.exact = slabs > 0 && slabs <= kExactSlabs && total < 0xffffu;
+  w.n = slabs <= 0 ? 0u : (w.exact ? total : (uint32_t)slabs * (uint32_t)(W1 * W2));
+  w.inv_w12 = 1.0f / (float)(W1 * W2);
+  w.inv_w2 = 1.0f / (float)W2;
 }
 
-// A walk as four float4s in shared memory (plus the clip normals in two more):
+// A walk as five float4s in shared memory (plus the clip normals in two more):
 //   w0 = (a, s1), w1 = (b, s2), w2 = (rho1, rho2, lo_m, hi_m),
 //   w3 = (1 / (W1 W2), 1 / W2, bits, first candidate number of the warp),
-//   bits = m | c0 << 2 | W1 << 11 | W2 << 19 | clip flags << 27.
+//   w4 = cumulative counts after slabs 0..7, 16 bits each (exact decode),
+//   bits = m | c0 << 2 | W1 << 11 | W2 << 19 | clip flags << 27 | exact << 29.
 // W1, W2 <= 2 + |s_k| + 2 rho_k < 16 since radius <= 4, and c0 < 512.
 struct PackedWalk {
   float4 w0, w1, w2, w3;
+  uint4 w4;
 };
 
 __device__ __forceinline__ PackedWalk pack_walk(const Walk& w, uint32_t clip, uint32_t first) {
@@ -106,29 +132,45 @@ __device__ __forceinline__ PackedWalk pack_walk(const Walk& w, uint32_t clip, ui
   p.w1 = make_float4(w.b.x, w.b.y, w.b.z, w.s2);
   p.w2 = make_float4(w.rho1, w.rho2, w.lo_m, w.hi_m);
   const uint32_t bits = (uint32_t)w.m | ((uint32_t)w.c0 << 2) | ((uint32_t)w.W1 << 11) |
-                        ((uint32_t)w.W2 << 19) | (clip << 27);
+                        ((uint32_t)w.W2 << 19) | (clip << 27) | ((uint32_t)w.exact << 29);
   p.w3 = make_float4(w.inv_w12, w.inv_w2, __uint_as_float(bits), __uint_as_float(first));
+  p.w4 = make_uint4(w.pre[0], w.pre[1], w.pre[2], w.pre[3]);
   return p;
 }
 
 // Candidate q of a packed walk: its voxel, or false when q falls outside its
-// slab's box.
+// slab's box (uniform decode only).
 __device__ __forceinline__ bool decode_candidate(const PackedWalk& p, int n, uint32_t q, int& x,
                                                  int& y, int& z) {
   const uint32_t bits = __float_as_uint(p.w3.z);
   const int m = bits & 3, c0 = (bits >> 2) & 511, W1 = (bits >> 11) & 255, W2 = (bits >> 19) & 255;
-  // (q + 1/2) / w is at least 1/(2w) from an integer, far beyond fp32 error for
-  // these small counts, so truncation gives the exact quotient
-  const int slab = (int)(((float)q + 0.5f) * p.w3.x);
-  const int rem = (int)q - slab * (W1 * W2);
-  const int dj = (int)(((float)rem + 0.5f) * p.w3.y);
-  const int dl = rem - dj * W2;
-  const int c = c0 + slab;
   const float am = m == 0 ? p.w0.x : (m == 1 ? p.w0.y : p.w0.z);
   const float a1 = m == 0 ? p.w0.y : p.w0.x;
   const float a2 = m == 2 ? p.w0.y : p.w0.z;
+  // (q + 1/2) / w is at least 1/(2w) from an integer, far beyond fp32 error for
+  // these small counts, so truncation gives the exact quotient
+  int slab, rem;
+  if (bits & (1u << 29)) {  // exact: the slab whose cumulative range holds q
+    const uint32_t pre[4] = {p.w4.x, p.w4.y, p.w4.z, p.w4.w};
+    slab = 0;
+    uint32_t base = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t v = (pre[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+      if (v <= q) { slab = k + 1; base = v; }
+    }
+    rem = (int)(q - base);
+  } else {
+    slab = (int)(((float)q + 0.5f) * p.w3.x);
+    rem = (int)q - slab * (W1 * W2);
+  }
+  const int c = c0 + slab;
   int j0, j1, l0, l1;
   slab_box(am, a1, a2, p.w0.w, p.w1.w, p.w2.x, p.w2.y, p.w2.z, p.w2.w, n, c, j0, j1, l0, l1);
+  const int w2 = (bits & (1u << 29)) ? l1 - l0 + 1 : W2;
+  const float inv_w2 = (bits & (1u << 29)) ? __frcp_rn((float)w2) : p.w3.y;
+  const int dj = (int)(((float)rem + 0.5f) * inv_w2);
+  const int dl = rem - dj * w2;
   const int j = j0 + dj, l = l0 + dl;
   if (j > j1 || l > l1) return false;
   x = m == 0 ? c : j;
