@@ -264,13 +264,13 @@ def run_ours(args, rank, world, local_rank):
     rgba_host = torch.empty_like(rgba, device="cpu").pin_memory()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
+    vrt.set_option(r.h, vrt.OPT_GRAPH, 0 if args.no_graph else 1)
+
     def frame(f, host=False):
+        # one call per frame: update, voxelize, pyramid (AO only), cull, trace;
+        # replayed as a CUDA graph unless --no-graph
         first, blk = (upd_host if host else upd_dev)[f % n_upd]
-        vrt.update_vertices(r.h, first, blk)
-        vrt.voxelize(r.h)
-        vrt.build_mips(r.h)
-        vrt.cull(r.h, c, p)
-        vrt.trace(r.h, c, p, rgba, fid, ft)
+        vrt.frame(r.h, c, p, rgba, fid, ft, first_vertex=first, update=blk)
 
     with torch.cuda.stream(stream):
         for f in range(args.warmup):
@@ -369,6 +369,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else "")
                    + (f" [occupancy pyramid in {args.mips}]" if args.mips != "fp32" else ""),
                    "l2": "flushed between frames (512 MB write)",
+                   "cuda_graph": not args.no_graph,
                    "segments": ls.n_segments, "grid": ls.n, "pixels": px,
                    "p50_ms": round(srt[len(srt) // 2], 4),
                    "p99_ms": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4),
@@ -522,6 +523,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="issue the frame's launches one by one instead of replaying a CUDA graph")
     ap.add_argument("--mips", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="storage of the occupancy pyramid (AO workloads)")
     ap.add_argument("--scale", type=float, default=1.0,

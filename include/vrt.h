@@ -211,15 +211,45 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
  * (default), VRT_MIPS_F16 or VRT_MIPS_BF16; every level is averaged in fp32
  * from its stored children and rounded to nearest once, and the trace widens
  * the samples to fp32. Changing it invalidates the pyramid (vrt_build_mips
- * again). vrt_read_mips returns the stored values widened to fp32. */
+ * again). vrt_read_mips returns the stored values widened to fp32.
+ * VRT_OPT_GRAPH (5): value 1 makes vrt_frame run as a CUDA graph (see there). */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
 #define VRT_OPT_TRACE_COUNTERS 3
 #define VRT_OPT_MIPS_FORMAT 4
+#define VRT_OPT_GRAPH 5
 #define VRT_MIPS_F32 0
 #define VRT_MIPS_F16 1
 #define VRT_MIPS_BF16 2
 vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value);
+
+/* One frame in one call: the vertex update (when n_vertices > 0; same rules as
+ * vrt_update_vertices), vrt_voxelize, vrt_build_mips when p->ao_cones, vrt_cull
+ * and vrt_trace. With VRT_OPT_GRAPH on, the chain is captured (on a stream the
+ * grid owns) into a CUDA graph that is launched on the grid's stream; the
+ * executable graph is updated in place from each frame's capture, so cameras,
+ * parameters and updates may change freely, and is re-instantiated when the
+ * launch sequence changes shape. Buffers the chain sizes lazily are allocated
+ * before the capture (this may synchronize the grid's stream). Frames with
+ * pageable host input run uncaptured. Stage timing works in both forms. The
+ * result is that of the separate calls. */
+vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const float* xyz,
+                     int32_t stride, int32_t on_device, const vrt_camera* cam,
+                     const vrt_render_params* p, float* rgba_out, int32_t* first_id_out,
+                     float* first_t_out);
+
+/* Autotuning of the voxel resolution: renders the scene (host vertices in the
+ * units of a grid of side base->n, camera in the same units) in grids of each
+ * side in `sides` -- coordinates, radius and camera scaled with the side -- for
+ * `frames` frames after a warm-up, and returns the side with the lowest mean
+ * frame time in *best_side (ms_out[i]: its mean time, +inf when that side
+ * could not render the scene). Without AO the image does not depend on the
+ * side beyond fp32 rounding at voxel boundaries. */
+vrt_status vrt_tune_grid_side(const vrt_grid_desc* base, const float* xyz, int32_t stride,
+                              int64_t n_vertices, const int64_t* polyline_offsets,
+                              int64_t n_polylines, const vrt_camera* cam,
+                              const vrt_render_params* p, const int32_t* sides, int32_t n_sides,
+                              int32_t frames, int32_t* best_side, float* ms_out);
 
 /* Device memory the grid holds, in bytes (its buffers as currently sized). */
 vrt_status vrt_grid_device_bytes(vrt_grid g, uint64_t* bytes);

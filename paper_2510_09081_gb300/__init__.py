@@ -25,6 +25,7 @@ OPT_FORCE_EXACT = 1
 OPT_STAGE_TIMING = 2
 OPT_TRACE_COUNTERS = 3
 OPT_MIPS_FORMAT = 4
+OPT_GRAPH = 5
 MIPS_F32, MIPS_F16, MIPS_BF16 = 0, 1, 2
 STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
 
@@ -34,7 +35,8 @@ SYMBOLS = ["vrt_create_grid", "vrt_upload_segments", "vrt_update_vertices", "vrt
            "vrt_read_grid", "vrt_read_lists", "vrt_read_mips", "vrt_set_option",
            "vrt_get_stage_ms", "vrt_scan_counts_noalloc", "vrt_last_error", "vrt_destroy",
            "vrt_grid_device_bytes", "vrt_set_stream", "vrt_server_create", "vrt_server_add_set",
-           "vrt_server_submit", "vrt_server_poll", "vrt_server_get_stats", "vrt_server_destroy"]
+           "vrt_server_submit", "vrt_server_poll", "vrt_server_get_stats", "vrt_server_destroy",
+           "vrt_frame", "vrt_tune_grid_side"]
 
 
 class VrtError(RuntimeError):
@@ -117,6 +119,11 @@ def load():
         "vrt_scan_counts_noalloc": [P, P, P, u64, P, P, P],
         "vrt_destroy": [P],
         "vrt_grid_device_bytes": [P, ctypes.POINTER(u64)],
+        "vrt_frame": [P, i64, i64, P, i32, i32, ctypes.POINTER(CameraC),
+                      ctypes.POINTER(RenderParamsC), P, P, P],
+        "vrt_tune_grid_side": [ctypes.POINTER(GridDesc), P, i32, i64, P, i64,
+                               ctypes.POINTER(CameraC), ctypes.POINTER(RenderParamsC), P, i32, i32,
+                               ctypes.POINTER(i32), P],
         "vrt_set_stream": [P, P],
         "vrt_server_create": [ctypes.POINTER(ServerDesc), ctypes.POINTER(P)],
         "vrt_server_add_set": [P, ctypes.POINTER(GridDesc), P, i32, i64, P, i64,
@@ -426,3 +433,37 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def frame(g, cam_c, params, rgba, first_id=None, first_t=None, first_vertex=0, update=None):
+    """vrt_frame: update (optional) + voxelize + mips (AO) + cull + trace."""
+    if update is None:
+        upd, n, stride, dev = None, 0, 3, 0
+    else:
+        dev = _is_device(update)
+        if hasattr(update, "data_ptr"):  # torch tensor (device, or pinned host memory: captured)
+            if str(update.dtype) != "torch.float32" or not update.is_contiguous():
+                raise ValueError("update must be a contiguous float32 tensor")
+            upd = update
+        else:
+            upd = np.ascontiguousarray(update, dtype=np.float32)
+        n, stride = int(upd.shape[0]), int(upd.shape[1])
+    _check(load().vrt_frame(g, int(first_vertex), n, _ptr(upd) if upd is not None else None, stride,
+                            int(dev), ctypes.byref(cam_c), ctypes.byref(params), _ptr(rgba),
+                            _ptr(first_id) if first_id is not None else None,
+                            _ptr(first_t) if first_t is not None else None), g)
+
+
+def tune_grid_side(xyz, offsets, n, radius, cam, sides, alpha=1.0, ao_cones=0, cull_on=0, frames=3):
+    """vrt_tune_grid_side: (best side, {side: mean ms})."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    desc = GridDesc(n=int(n), radius=float(radius), r_min=0.5, occ_scale=32, max_fragments=0)
+    sides_a = np.ascontiguousarray(sides, dtype=np.int32)
+    ms = np.zeros(sides_a.shape[0], np.float32)
+    best = ctypes.c_int32(0)
+    _check(load().vrt_tune_grid_side(ctypes.byref(desc), _ptr(xyz), int(xyz.shape[1]), int(xyz.shape[0]),
+                                     _ptr(offsets), int(offsets.shape[0] - 1), ctypes.byref(camera_c(cam)),
+                                     ctypes.byref(params_c(alpha, ao_cones, cull_on, 0)), _ptr(sides_a),
+                                     int(sides_a.shape[0]), int(frames), ctypes.byref(best), _ptr(ms)))
+    return int(best.value), {int(k): float(v) for k, v in zip(sides_a, ms)}

@@ -68,6 +68,13 @@ struct vrt_grid_s {
   // seen on the host (-1: not yet), and list builds since the last cull
   double auto_vis_frac = -1.0;
   int auto_skipped = 0;
+  // vrt_frame as a CUDA graph: the executable graph (updated in place while
+  // the frame's launch sequence keeps its shape) and the grid's own stream the
+  // frame is captured on (the legacy default stream cannot be captured)
+  bool use_graph = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;
   std::string err;
   // device memory held by this grid
   std::unordered_map<void*, size_t> alloc_bytes;
@@ -264,7 +271,10 @@ enum { ST_INGEST, ST_PASS1, ST_MIPS, ST_CULL, ST_SCAN, ST_PASS2, ST_TRACE, ST_RE
 
 void stage_mark(vrt_grid g, int stage, int end) {
   if (!g->timing) return;
-  cudaEventRecord(g->ev[stage][end], g->stream);
+  // inside a capture the record becomes an event node, so the replayed graph
+  // still times its stages
+  cudaEventRecordWithFlags(g->ev[stage][end], g->stream,
+                           g->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   if (end) g->ev_used[stage] = true;
 }
 
@@ -286,6 +296,14 @@ vrt_status size_exact_queue(vrt_grid g) {
 }
 
 void free_all(vrt_grid g) {
+  if (g->graph_exec) {
+    cudaGraphExecDestroy(g->graph_exec);
+    g->graph_exec = nullptr;
+  }
+  if (g->cap_stream) {
+    cudaStreamDestroy(g->cap_stream);
+    g->cap_stream = nullptr;
+  }
   for (int i = 0; i < VRT_N_STAGES; ++i)
     for (int j = 0; j < 2; ++j)
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
@@ -742,6 +760,152 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats) {
   return VRT_OK;
 }
 
+vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const float* xyz,
+                     int32_t stride, int32_t on_device, const vrt_camera* cam,
+                     const vrt_render_params* p, float* rgba, int32_t* first_id, float* first_t) {
+  if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (!cam || !p || !rgba) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  auto chain = [&]() -> vrt_status {
+    vrt_status r = VRT_OK;
+    if (n_vertices > 0) r = vrt_update_vertices(g, first_vertex, n_vertices, xyz, stride, on_device);
+    if (r == VRT_OK) r = vrt_voxelize(g);
+    if (r == VRT_OK && p->ao_cones) r = vrt_build_mips(g);
+    if (r == VRT_OK) r = vrt_cull(g, cam, p);
+    if (r == VRT_OK) r = vrt_trace(g, cam, p, rgba, first_id, first_t);
+    return r;
+  };
+  if (!g->use_graph || g->stage < 1) return chain();
+  // pageable host input cannot be captured (its copy is synchronous)
+  if (n_vertices > 0 && !on_device) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, xyz) != cudaSuccess || at.type == cudaMemoryTypeUnregistered) {
+      cudaGetLastError();
+      return chain();
+    }
+  }
+  // every buffer the chain sizes lazily exists before the capture (no
+  // allocation may happen inside one)
+  const size_t nv = (size_t)g->n * g->n * g->n;
+  if (p->ao_cones && !g->mips) VRT_CUDA(g, dalloc(g, (float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  if (p->cull) {
+    if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
+    if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
+    if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
+    const uint32_t npx = (uint32_t)cam->width * (uint32_t)cam->height;
+    if (npx > g->pq_cap) {
+      VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+      dfree(g, g->pq[0]); dfree(g, g->pq[1]); dfree(g, g->resume);
+      g->pq_cap = 0;
+      VRT_CUDA(g, dalloc(g, &g->pq[0], npx));
+      VRT_CUDA(g, dalloc(g, &g->pq[1], npx));
+      VRT_CUDA(g, dalloc(g, &g->resume, 2 * (size_t)npx));
+      g->pq_cap = npx;
+    }
+  }
+  if (!g->cap_stream) VRT_CUDA(g, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = g->stream;
+  g->stream = g->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  vrt_status r = VRT_OK;
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) {
+    g->capturing = true;
+    r = chain();
+    g->capturing = false;
+    e = cudaStreamEndCapture(g->stream, &graph);
+  }
+  g->stream = user;
+  if (r != VRT_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (r != VRT_OK) return r;
+    return cuda_fail(g, e, "stream capture of the frame");
+  }
+  if (g->graph_exec) {  // same launch sequence as last frame: update the parameters in place
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(g->graph_exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(g->graph_exec);
+      g->graph_exec = nullptr;
+    }
+  }
+  cudaError_t ie = cudaSuccess;
+  if (!g->graph_exec) ie = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return cuda_fail(g, ie, "cudaGraphInstantiate");
+  VRT_CUDA(g, cudaGraphLaunch(g->graph_exec, g->stream));
+  return VRT_OK;
+}
+
+vrt_status vrt_tune_grid_side(const vrt_grid_desc* base, const float* xyz, int32_t stride,
+                              int64_t n_vertices, const int64_t* offsets, int64_t n_polylines,
+                              const vrt_camera* cam, const vrt_render_params* p,
+                              const int32_t* sides, int32_t n_sides, int32_t frames,
+                              int32_t* best_side, float* ms_out) {
+  if (!base || !xyz || !offsets || !cam || !p || !sides || n_sides <= 0 || frames <= 0 || !best_side)
+    return fail(nullptr, VRT_ERR_INVALID_ARG, "NULL argument or empty candidate list");
+  if (stride != 3 && stride != 4) return fail(nullptr, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  float best = INFINITY;
+  *best_side = 0;
+  std::vector<float> scaled((size_t)n_vertices * 3);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  VRT_CUDA(nullptr, cudaEventCreate(&e0));
+  VRT_CUDA(nullptr, cudaEventCreate(&e1));
+  vrt_status result = VRT_OK;
+  float* out = nullptr;
+  const size_t npx = (size_t)cam->width * cam->height;
+  if (cudaMalloc((void**)&out, npx * 4 * sizeof(float)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(nullptr, VRT_ERR_OOM, "output buffer");
+  }
+  for (int32_t i = 0; i < n_sides && result == VRT_OK; ++i) {
+    // the same scene in a grid of side sides[i]: coordinates, radius and camera
+    // scale with the side
+    const double f = (double)sides[i] / (double)base->n;
+    for (int64_t v = 0; v < n_vertices; ++v)
+      for (int k = 0; k < 3; ++k) scaled[3 * v + k] = (float)(xyz[v * stride + k] * f);
+    vrt_grid_desc d = *base;
+    d.n = sides[i];
+    d.radius = (float)(base->radius * f);
+    vrt_camera c = *cam;
+    for (int k = 0; k < 3; ++k) {
+      c.eye[k] = (float)(cam->eye[k] * f);
+      c.target[k] = (float)(cam->target[k] * f);
+    }
+    c.ortho_h = (float)(cam->ortho_h * f);
+    vrt_grid g = nullptr;
+    float ms = INFINITY;
+    vrt_status r = vrt_create_grid(&d, nullptr, &g);
+    if (r == VRT_OK) r = vrt_upload_segments(g, scaled.data(), 3, n_vertices, offsets, n_polylines, 0);
+    if (r == VRT_OK) r = vrt_frame(g, 0, 0, nullptr, 3, 0, &c, p, out, nullptr, nullptr);  // warm-up
+    if (r == VRT_OK) r = vrt_sync(g);
+    if (r == VRT_OK) {
+      cudaEventRecord(e0, nullptr);
+      for (int32_t k = 0; k < frames && r == VRT_OK; ++k)
+        r = vrt_frame(g, 0, 0, nullptr, 3, 0, &c, p, out, nullptr, nullptr);
+      cudaEventRecord(e1, nullptr);
+      cudaEventSynchronize(e1);
+      if (r == VRT_OK) r = vrt_sync(g);
+      if (r == VRT_OK) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)frames;
+      }
+    }
+    if (g) vrt_destroy(g);
+    if (r != VRT_OK) ms = INFINITY;  // a side that does not work (range, memory) is skipped
+    if (ms_out) ms_out[i] = ms;
+    if (ms < best) {
+      best = ms;
+      *best_side = sides[i];
+    }
+  }
+  cudaFree(out);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (*best_side == 0) return fail(nullptr, VRT_ERR_INVALID_ARG, "no candidate side rendered the scene");
+  return result;
+}
+
 vrt_status vrt_grid_device_bytes(vrt_grid g, uint64_t* bytes) {
   if (!g || !bytes) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
   *bytes = g->dev_bytes;
@@ -762,6 +926,10 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
   }
   if (option == VRT_OPT_TRACE_COUNTERS) {
     g->trace_counters = value ? 1 : 0;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_GRAPH) {
+    g->use_graph = value != 0;
     return VRT_OK;
   }
   if (option == VRT_OPT_MIPS_FORMAT) {

@@ -2,7 +2,8 @@
 sets): every served frame equals, bitwise, the same frame rendered alone
 through the plain calls on a grid that saw the same updates in the same order,
 with several frames on the device at once and with sets evicted and uploaded
-again under a small HBM budget."""
+again under a small HBM budget. Also the one-call frame as a CUDA graph
+(equal to the separate calls) and the grid-side autotuner."""
 import numpy as np
 import pytest
 
@@ -143,3 +144,41 @@ def test_server_errors():
     res = srv.poll(wait=True)
     assert len(res) == 1 and res[0]["status"] == vrt.ERR_OOM
     srv.close()
+
+
+def test_graph_frames_equal_separate_calls():
+    sets = _sets()
+    ls = sets[1]
+    reqs = [q for q in _requests([ls], 12, seed=7)]
+    for q in reqs:  # the same image size throughout, so frames after the first are captured
+        q["cam"] = _camera(np.random.default_rng(len(q)), ls.n, 80, 60)
+    alone = _plain([ls], reqs)
+    r = vrt.Renderer(ls.n, ls.radius)
+    r.upload(ls.xyz, ls.offsets)
+    vrt.set_option(r.h, vrt.OPT_GRAPH, 1)
+    got = []
+    for q in reqs:
+        c = vrt.camera_c(q["cam"])
+        rgba = torch.zeros((c.height, c.width, 4), device="cuda")
+        fid = torch.zeros((c.height, c.width), dtype=torch.int32, device="cuda")
+        ft = torch.zeros((c.height, c.width), device="cuda")
+        upd = q["update"]
+        if upd is not None and len(got) % 3 == 0:
+            upd = torch.from_numpy(upd).cuda()
+        elif upd is not None and len(got) % 3 == 1:
+            upd = torch.from_numpy(upd).pin_memory()  # pageable numpy otherwise (runs uncaptured)
+        vrt.frame(r.h, c, vrt.params_c(q["alpha"], q["ao"], q["cull"]), rgba, fid, ft,
+                  first_vertex=q["first"], update=upd)
+        vrt.sync(r.h)
+        got.append((rgba.cpu().numpy(), fid.cpu().numpy(), ft.cpu().numpy()))
+    r.close()
+    _assert_equal(got, alone)
+
+
+def test_tune_grid_side():
+    ls = _sets()[0]
+    cam = _camera(np.random.default_rng(3), ls.n, 96, 64)
+    best, ms = vrt.tune_grid_side(ls.xyz, ls.offsets, ls.n, ls.radius, cam, [32, 64, 128], alpha=0.5)
+    assert best in (32, 64, 128)
+    assert all(np.isfinite(v) and v > 0 for v in ms.values())
+    assert ms[best] == min(ms.values())
