@@ -21,7 +21,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 # Parity bands for an fp32 implementation, in the units of the quantity they
-# bound ("parity readings"):
+# bound:
 #   tie:   two depths closer than tie_abs + tie_rel * t may come out in either order
 #   graze: |discriminant| / r^2 below graze_rel may flip hit <-> miss
 #   pos:   hit points within pos_abs + pos_rel * t of a clip plane or the grid
@@ -50,7 +50,17 @@ class _Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("ao_cones", ctypes.c_int32),
                 ("tie_rel", ctypes.c_double), ("tie_abs", ctypes.c_double),
                 ("graze_rel", ctypes.c_double), ("pos_abs", ctypes.c_double),
-                ("pos_rel", ctypes.c_double)]
+                ("pos_rel", ctypes.c_double), ("voxel_shading", ctypes.c_int32),
+                ("light", ctypes.c_float * 3)]
+
+
+def _prm(alpha, ao_cones, bands, voxel_shading, light):
+    b = dict(DEFAULT_BANDS)
+    if bands:
+        b.update(bands)
+    prm = _Params(alpha=float(alpha), ao_cones=int(ao_cones), voxel_shading=int(voxel_shading), **b)
+    prm.light[:] = [float(v) for v in light]
+    return prm
 
 
 def _load():
@@ -73,6 +83,8 @@ def _load():
     lib.or_build_mips.argtypes = [P, P]
     lib.or_ao.restype = f64
     lib.or_ao.argtypes = [P, P]
+    lib.or_voxel_shade.restype = f64
+    lib.or_voxel_shade.argtypes = [P, i64, i64, i64, i32, P]
     lib.or_render.restype = i32
     lib.or_render.argtypes = [P, ctypes.POINTER(_Cam), ctypes.POINTER(_Params), i32, i64, i64,
                               P, P, P, P, P, P]
@@ -200,14 +212,17 @@ class Oracle:
         p = np.ascontiguousarray(p, dtype=np.float64)
         return float(_load().or_ao(self._h, _ptr(p)))
 
+    def voxel_shade(self, x, y, z, light, ao_cones=0):
+        """Voxel-space shading value at the centre of voxel (x, y, z) (Sec. 3.4):
+        AO (when ao_cones) times 1/2 + 1/2 * shadow transmittance toward light."""
+        lt = np.ascontiguousarray(light, dtype=np.float32)
+        return float(_load().or_voxel_shade(self._h, int(x), int(y), int(z), int(ao_cones), _ptr(lt)))
+
     # --------------------------------------------------------------- render
     def render(self, cam, alpha=1.0, ao_cones=0, brute=False, pix_begin=0, pix_end=None,
-               bands=None):
+               bands=None, voxel_shading=0, light=(0.0, 0.0, 1.0)):
         lib = _load()
-        b = dict(DEFAULT_BANDS)
-        if bands:
-            b.update(bands)
-        prm = _Params(alpha=float(alpha), ao_cones=int(ao_cones), **b)
+        prm = _prm(alpha, ao_cones, bands, voxel_shading, light)
         c = _cam(cam)
         npx = cam.width * cam.height
         pix_end = npx if pix_end is None else pix_end
@@ -236,13 +251,11 @@ class Oracle:
         lib.or_voxel_fragments(self._h, int(x), int(y), int(z), _ptr(ids), n, _ptr(occ))
         return ids[:n], tuple(int(v) for v in occ)
 
-    def render_pixels(self, cam, pix, alpha=1.0, ao_cones=0, brute=False, bands=None):
+    def render_pixels(self, cam, pix, alpha=1.0, ao_cones=0, brute=False, bands=None,
+                      voxel_shading=0, light=(0.0, 0.0, 1.0)):
         """Render the listed pixels (row-major indices); outputs as render()."""
         lib = _load()
-        b = dict(DEFAULT_BANDS)
-        if bands:
-            b.update(bands)
-        prm = _Params(alpha=float(alpha), ao_cones=int(ao_cones), **b)
+        prm = _prm(alpha, ao_cones, bands, voxel_shading, light)
         c = _cam(cam)
         pix = np.ascontiguousarray(pix, np.int64)
         n = pix.shape[0]

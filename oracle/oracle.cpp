@@ -26,7 +26,9 @@
 //                   it, sorted by (t, id) and composited front to back
 //                   ("ground-truth transparency", Sec. 3.5); optional cone-traced
 //                   ambient occlusion per hit (Sec. 3.4 cones over the occupancy
-//                   pyramid).
+//                   pyramid), or voxel-space shading (Sec. 3.4): ambient
+//                   occlusion and a directional shadow evaluated at voxel
+//                   centres, sampled trilinearly at each hit.
 //   * brute      -- the same image from all segments, no lists (pin for the
 //                   conservativeness claim of Sec. 3.5).
 //   * sampled    -- one voxel's fragments (list and occupancy codes) and a list
@@ -296,6 +298,8 @@ struct Camera {
 struct Params {
   double alpha;
   int ao_cones;
+  int voxel_shading;         // 1: shade from the voxel-space shading field
+  V3 light;                  // unit direction toward the light (voxel shading)
   double tie_rel, tie_abs;   // two depths tie if |ta - tb| <= tie_abs + tie_rel * max(|t|)
   double graze_rel;          // a ray grazes if |discriminant| / r^2 <= graze_rel
   double pos_abs, pos_rel;   // a hit point is within pos_abs + pos_rel * t of a clip
@@ -487,6 +491,46 @@ double ambient_occlusion(const Ctx& c, V3 P) {
   return 1.0 - sumA / 6.0;
 }
 
+// Voxel-space shading (Sec. 3.4, Shading): at the centre P of voxel (x, y, z),
+// ambient occlusion by the six cones above (when ao_cones is set) times a
+// directional shadow term 1/2 + S/2. S is the transmittance of a ray from P
+// toward the light through the base occupancy level: samples at P + k L for
+// k = 1, 2, ... (one voxel apart, so the voxel's own lines do not shadow it),
+// trilinear at texel centres, accumulated A <- A + (1 - A) s, S = 1 - A. The
+// march ends where a sample's texels all lie outside the grid (beyond half a
+// voxel past the boundary), so every sample that can be non-zero is taken.
+double voxel_shade(const Ctx& c, int64_t x, int64_t y, int64_t z, const Params& prm) {
+  const V3 P = {x + 0.5, y + 0.5, z + 0.5};
+  const double ao = prm.ao_cones ? ambient_occlusion(c, P) : 1.0;
+  const double lo = -0.5, hi = c.N + 0.5;
+  double A = 0;
+  for (int64_t k = 1;; ++k) {
+    const V3 q = P + (double)k * prm.light;
+    if (q.x < lo || q.x > hi || q.y < lo || q.y > hi || q.z < lo || q.z > hi) break;
+    A = A + (1 - A) * trilinear(c, 0, q);
+  }
+  return ao * (0.5 + 0.5 * (1.0 - A));
+}
+
+// The shading field at a hit point: trilinear over the voxel-centre values,
+// texel coordinates clamped to the grid (one texture sample per hit, Sec. 3.4).
+double shade_at(const Ctx& c, V3 P, const Params& prm) {
+  const double u[3] = {P.x - 0.5, P.y - 0.5, P.z - 0.5};
+  int64_t i0[3];
+  double f[3];
+  for (int k = 0; k < 3; ++k) { i0[k] = (int64_t)std::floor(u[k]); f[k] = u[k] - i0[k]; }
+  auto cl = [&](int64_t v) { return std::min<int64_t>(c.N - 1, std::max<int64_t>(0, v)); };
+  double acc = 0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+        if (w == 0) continue;
+        acc += w * voxel_shade(c, cl(i0[0] + dx), cl(i0[1] + dy), cl(i0[2] + dz), prm);
+      }
+  return acc;
+}
+
 // ------------------------------------------------------------------ rendering
 struct Ray { V3 o, d; };
 
@@ -575,8 +619,9 @@ struct PixelOut {
 };
 
 // Front-to-back compositing of the accepted hits in (t, id) order over
-// transparent black: premultiplied colour C += T * alpha * c * AO,
-// transmittance T *= 1 - alpha; output (C, 1 - T).
+// transparent black: premultiplied colour C += T * alpha * c * shade (shade =
+// AO per hit, the voxel-space shading field, or 1), transmittance
+// T *= 1 - alpha; output (C, 1 - T).
 void composite(const Ctx& c, const Ray& ray, const std::vector<Cand>& cs, int toggle,
                const Params& prm, double out[4]) {
   double C[3] = {0, 0, 0}, T = 1.0;
@@ -585,7 +630,8 @@ void composite(const Ctx& c, const Ray& ray, const std::vector<Cand>& cs, int to
     if (!use) continue;
     if (T < 1e-12) break;
     V3 col = seg_colour(c, cs[k].id);
-    if (prm.ao_cones) col = ambient_occlusion(c, ray.o + cs[k].t * ray.d) * col;
+    if (prm.voxel_shading) col = shade_at(c, ray.o + cs[k].t * ray.d, prm) * col;
+    else if (prm.ao_cones) col = ambient_occlusion(c, ray.o + cs[k].t * ray.d) * col;
     C[0] += T * prm.alpha * col.x;
     C[1] += T * prm.alpha * col.y;
     C[2] += T * prm.alpha * col.z;
@@ -783,7 +829,25 @@ struct or_params {
   float alpha;
   int32_t ao_cones;
   double tie_rel, tie_abs, graze_rel, pos_abs, pos_rel;
+  int32_t voxel_shading;
+  float light[3];  // direction toward the light (normalized here)
 };
+
+Params make_params(const or_params* p) {
+  Params prm;
+  prm.alpha = p->alpha; prm.ao_cones = p->ao_cones;
+  prm.tie_rel = p->tie_rel; prm.tie_abs = p->tie_abs;
+  prm.graze_rel = p->graze_rel;
+  prm.pos_abs = p->pos_abs; prm.pos_rel = p->pos_rel;
+  prm.voxel_shading = p->voxel_shading;
+  const V3 l = {p->light[0], p->light[1], p->light[2]};
+  prm.light = norm(l) > 0 ? normalize(l) : V3{0, 0, 1};
+  return prm;
+}
+
+void need_mips(Ctx* c) {
+  if (!c->have_mips) { if (!c->have_lists) build_lists(*c); build_mips(*c); }
+}
 
 // Returns 0 on success; 1 = bad grid side; 2 = coordinate out of range or not
 // finite; 3 = bad offsets; 4 = bad radius.
@@ -876,6 +940,19 @@ int64_t or_build_mips(void* h, double* out) {
   return (int64_t)c->mips.size();
 }
 
+// Voxel-space shading value at the centre of voxel (x, y, z).
+double or_voxel_shade(void* h, int64_t x, int64_t y, int64_t z, int32_t ao_cones,
+                      const float* light) {
+  Ctx* c = (Ctx*)h;
+  need_mips(c);
+  or_params p;
+  std::memset(&p, 0, sizeof(p));
+  p.ao_cones = ao_cones;
+  p.voxel_shading = 1;
+  for (int k = 0; k < 3; ++k) p.light[k] = light[k];
+  return voxel_shade(*c, x, y, z, make_params(&p));
+}
+
 double or_ao(void* h, const double* P) {
   Ctx* c = (Ctx*)h;
   if (!c->have_mips) { if (!c->have_lists) build_lists(*c); build_mips(*c); }
@@ -889,18 +966,14 @@ int32_t or_render(void* h, const or_camera* cam_in, const or_params* prm_in, int
                   int32_t* first_id, int32_t* first_id_alt, float* first_t, uint8_t* exempt) {
   Ctx* c = (Ctx*)h;
   if (!brute && !c->have_lists) build_lists(*c);
-  if (prm_in->ao_cones && !c->have_mips) { if (!c->have_lists) build_lists(*c); build_mips(*c); }
+  if (prm_in->ao_cones || prm_in->voxel_shading) need_mips(c);
   Camera cam;
   cam.width = cam_in->width; cam.height = cam_in->height; cam.ortho = cam_in->ortho;
   for (int k = 0; k < 3; ++k) {
     cam.eye[k] = cam_in->eye[k]; cam.target[k] = cam_in->target[k]; cam.up[k] = cam_in->up[k];
   }
   cam.fovy_deg = cam_in->fovy_deg; cam.ortho_h = cam_in->ortho_h;
-  Params prm;
-  prm.alpha = prm_in->alpha; prm.ao_cones = prm_in->ao_cones;
-  prm.tie_rel = prm_in->tie_rel; prm.tie_abs = prm_in->tie_abs;
-  prm.graze_rel = prm_in->graze_rel;
-  prm.pos_abs = prm_in->pos_abs; prm.pos_rel = prm_in->pos_rel;
+  const Params prm = make_params(prm_in);
   int64_t n = pix_end - pix_begin;
   parallel_for(n, c->nthreads, [&](int64_t j) {
     int64_t p = pix_begin + j;
@@ -963,18 +1036,14 @@ int32_t or_render_pixels(void* h, const or_camera* cam_in, const or_params* prm_
                          int32_t* first_id, int32_t* first_id_alt, float* first_t, uint8_t* exempt) {
   Ctx* c = (Ctx*)h;
   if (!brute && !c->have_lists) build_lists(*c);
-  if (prm_in->ao_cones && !c->have_mips) { if (!c->have_lists) build_lists(*c); build_mips(*c); }
+  if (prm_in->ao_cones || prm_in->voxel_shading) need_mips(c);
   Camera cam;
   cam.width = cam_in->width; cam.height = cam_in->height; cam.ortho = cam_in->ortho;
   for (int k = 0; k < 3; ++k) {
     cam.eye[k] = cam_in->eye[k]; cam.target[k] = cam_in->target[k]; cam.up[k] = cam_in->up[k];
   }
   cam.fovy_deg = cam_in->fovy_deg; cam.ortho_h = cam_in->ortho_h;
-  Params prm;
-  prm.alpha = prm_in->alpha; prm.ao_cones = prm_in->ao_cones;
-  prm.tie_rel = prm_in->tie_rel; prm.tie_abs = prm_in->tie_abs;
-  prm.graze_rel = prm_in->graze_rel;
-  prm.pos_abs = prm_in->pos_abs; prm.pos_rel = prm_in->pos_rel;
+  const Params prm = make_params(prm_in);
   parallel_for(n, c->nthreads, [&](int64_t j) {
     const int64_t p = pix[j];
     int px = (int)(p % cam.width), py = (int)(p / cam.width);

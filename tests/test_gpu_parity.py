@@ -323,7 +323,7 @@ def test_reduced_precision_ao_images(fmt):
     res = compare_image(rgba, fid, ft, ref, tol=tol)
     assert res["hits"] > 1000
     assert_image(res, max_exempt_frac=0.02)
-    # the error actually seen, against the primary fp64 result (stated in the design doc)
+    # the error actually seen, against the primary fp64 result
     ok = ((ref["exempt"] & 1) == 0) & (fid >= 0)
     d = np.abs(rgba - ref["rgba"]).max(1)[ok]
     print(f"fmt {fmt}: RGBA error vs fp64 oracle over {ok.sum()} hit pixels: "

@@ -527,6 +527,96 @@ def test_ao_single_wall():
     assert full[0].sum() > 0
 
 
+# ----------------------------------------------------------------------------
+# voxel-space shading (Sec. 3.4, Shading)
+# ----------------------------------------------------------------------------
+AXES = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+
+
+def _column_shadow(occ0, x, y, z, L):
+    """Transmittance from the centre of voxel (x, y, z) toward an axis light L:
+    with L along an axis every sample sits on a texel centre k voxels away, so
+    S is the product of (1 - occupancy) over the voxels strictly beyond this one
+    up to the grid boundary."""
+    n = occ0.shape[0]
+    S = 1.0
+    k = 1
+    while True:
+        u = (x + k * L[0], y + k * L[1], z + k * L[2])
+        if not all(0 <= c < n for c in u):
+            break
+        S *= 1.0 - occ0[u[2], u[1], u[0]]
+        k += 1
+    return S
+
+
+def test_voxel_shadow_closed_form_along_axes():
+    ls = tiny_walks(n_lines=150, n_verts=40, n=16, radius=0.6, seed=41)
+    o = oracle.Oracle.from_lineset(ls)
+    occ0 = o.mips()[0]
+    assert 0.05 < (occ0 > 0).mean() < 0.9
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(60):
+        x, y, z = (int(v) for v in rng.integers(0, 16, 3))
+        for L in AXES:
+            S = _column_shadow(occ0, x, y, z, L)
+            assert o.voxel_shade(x, y, z, L) == pytest.approx(0.5 + 0.5 * S, abs=1e-12)
+            checked += S < 0.999
+    assert checked > 50  # most columns are shadowed by something
+    # with ambient occlusion: the cone AO at the voxel centre times the same term
+    for _ in range(10):
+        x, y, z = (int(v) for v in rng.integers(0, 16, 3))
+        S = _column_shadow(occ0, x, y, z, (0, 0, -1))
+        ao = o.ao((x + 0.5, y + 0.5, z + 0.5))
+        assert o.voxel_shade(x, y, z, (0, 0, -1), ao_cones=6) == pytest.approx(ao * (0.5 + 0.5 * S),
+                                                                               abs=1e-12)
+
+
+def test_voxel_shadow_empty_full_and_boundary():
+    """Empty grid: no shadow (1). Full grid: the first sample, one voxel toward
+    the light, is fully occupied (1/2), except where that sample's texels are
+    all outside the grid (1); any unnormalized light direction gives the same."""
+    o = oracle.Oracle(np.array([[1, 1, 1], [1.5, 1, 1]], np.float32), np.array([0, 2]), 16, 0.1)
+    assert o.voxel_shade(10, 10, 10, (0.3, -0.2, 0.9)) == 1.0
+    o = _full_grid(16)
+    assert o.voxel_shade(7, 7, 7, (0.3, -0.2, 0.9)) == pytest.approx(0.5, abs=1e-12)
+    assert o.voxel_shade(14, 3, 3, (1, 0, 0)) == pytest.approx(0.5, abs=1e-12)
+    assert o.voxel_shade(15, 3, 3, (1, 0, 0)) == pytest.approx(1.0, abs=1e-12)
+    assert o.voxel_shade(15, 3, 3, (-2, 0, 0)) == pytest.approx(0.5, abs=1e-12)
+    assert o.voxel_shade(0, 3, 3, (-1, 0, 0)) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_render_samples_the_voxel_shading_at_the_hit():
+    """A tube along x whose top passes through the centre of voxel (5, 8, 4),
+    seen from above through that centre: the opaque hit lies on the centre, so
+    the colour is the tangent colour (1, 0, 0) times that voxel's shading; a hit
+    on the face between two voxel centres gets the mean of the two."""
+    r = 0.5
+    zc = 4.5 - r
+    xyz = np.array([[2.0, 8.5, zc], [12.0, 8.5, zc], [2.0, 3.5, 1.5], [5.0, 3.5, 13.5]], np.float32)
+    o = oracle.Oracle(xyz, np.array([0, 2, 4]), 16, r)
+    light = (0.0, 0.0, -1.0)  # below: through the tube itself
+    out = o.render(_ortho_down(5.5, 8.5), alpha=1.0, voxel_shading=1, light=light)
+    assert out["first_id"][0] == 0
+    assert out["first_t"][0] == pytest.approx(10 - 4.5, abs=1e-6)
+    sh = o.voxel_shade(5, 8, 4, light)
+    assert sh < 0.9  # the tube shadows the centre
+    assert np.allclose(out["rgba"][0], (sh, 0, 0, 1), atol=1e-6)
+    # the top of the end ball at x = 12 lies on the face between voxels 11 and
+    # 12, whose columns below differ (tube body vs end cap)
+    out = o.render(_ortho_down(12.0, 8.5), alpha=1.0, voxel_shading=1, light=light)
+    assert out["first_t"][0] == pytest.approx(10 - 4.5, abs=1e-6)
+    s11, s12 = o.voxel_shade(11, 8, 4, light), o.voxel_shade(12, 8, 4, light)
+    assert abs(s11 - s12) > 0.01
+    assert np.allclose(out["rgba"][0], (0.5 * (s11 + s12), 0, 0, 1), atol=1e-6)
+    # the light from above: nothing above the tube, the centre is unshadowed
+    out = o.render(_ortho_down(5.5, 8.5), alpha=1.0, voxel_shading=1, light=(0, 0, 1))
+    assert np.allclose(out["rgba"][0], (1, 0, 0, 1), atol=1e-6)
+    # without voxel shading the same pixel is the plain tangent colour
+    assert np.allclose(o.render(_ortho_down(5.5, 8.5), alpha=1.0)["rgba"][0], (1, 0, 0, 1))
+
+
 # ------------------------------------------------------------- sampled queries
 def test_voxel_fragments_equal_the_list_build():
     # the per-voxel brute-force query (for sets too large for a full build)
