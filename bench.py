@@ -142,12 +142,14 @@ def stage_bytes(stage, n, V, st, px):
         "pass2": 16 * V + 4 * Fv + 4 * N3,             # pos in, list entries + cursors out
         "trace": 24 * px,                              # rgba + first id + first depth out
         "repair": 0,
+        "shade": 4 * N3 + N3 // 8 + N3 // 8,           # words + marks read, field mask written
     }[stage]
 
 
 # The trace kernel is bound by instruction issue and latency, not by DRAM: its
 # roofline counts the method's FP32 work, one ray-capsule entry test per list
 # entry a ray examines, against the FP32 rate of the SMs.
+SHADING_LIGHT = (0.4, 0.5, 0.77)  # direction toward the light for --shading voxel
 TRACE_FLOPS_PER_ENTRY = 82        # FP32 operations of one capsule entry test
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -257,7 +259,8 @@ def run_ours(args, rank, world, local_rank):
     vrt.set_option(r.h, vrt.OPT_MIPS_FORMAT, {"fp32": vrt.MIPS_F32, "fp16": vrt.MIPS_F16,
                                               "bf16": vrt.MIPS_BF16}[args.mips])
     c = vrt.camera_c(cam)
-    p = vrt.params_c(alpha=wl["alpha"], ao_cones=wl["ao"], cull=wl["cull"])
+    p = vrt.params_c(alpha=wl["alpha"], ao_cones=wl["ao"], cull=wl["cull"],
+                     voxel_shading=1 if args.shading == "voxel" else 0, light=SHADING_LIGHT)
     rgba = torch.empty((cam.height, cam.width, 4), dtype=torch.float32, device=dev)
     fid = torch.empty((cam.height, cam.width), dtype=torch.int32, device=dev)
     ft = torch.empty((cam.height, cam.width), dtype=torch.float32, device=dev)
@@ -367,7 +370,9 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "impl": "ours",
         "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else "")
-                   + (f" [occupancy pyramid in {args.mips}]" if args.mips != "fp32" else ""),
+                   + (f" [occupancy pyramid in {args.mips}]" if args.mips != "fp32" else "")
+                   + (f" [voxel-space shading: AO x shadow toward {SHADING_LIGHT}]"
+                      if args.shading == "voxel" else ""),
                    "l2": "flushed between frames (512 MB write)",
                    "cuda_graph": not args.no_graph,
                    "segments": ls.n_segments, "grid": ls.n, "pixels": px,
@@ -527,6 +532,9 @@ def main():
                     help="issue the frame's launches one by one instead of replaying a CUDA graph")
     ap.add_argument("--mips", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="storage of the occupancy pyramid (AO workloads)")
+    ap.add_argument("--shading", choices=("hit", "voxel"), default="hit",
+                    help="hit: the workload's per-hit shading; voxel: voxel-space shading field "
+                         "(AO when the workload has it, and a directional shadow)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="fraction of the bundle streamlines (small cases for profiler captures)")
     args = ap.parse_args()

@@ -101,6 +101,18 @@ typedef struct {
                        keeps 4 nearest keys per lane (128 per warp) and
                        rescans a list when it must, so the image does not
                        depend on k */
+  int32_t voxel_shading; /* 0: shade per hit (ao_cones); 1: voxel-space
+                       shading (Sec. 3.4): before the trace, every voxel
+                       within one step of a listed voxel gets the value
+                       AO(centre) * (1/2 + 1/2 * S), AO the six-cone occlusion
+                       at the voxel centre when ao_cones = 6 (else 1) and S the
+                       transmittance of a ray from the centre toward the light
+                       through the base pyramid level (samples one voxel
+                       apart from one voxel out, trilinear, A <- A + (1-A)s,
+                       S = 1 - A; the march may stop once S < 1e-4); each hit
+                       is shaded by one trilinear sample of that field */
+  float light[3];   /* voxel_shading: direction toward the directional light
+                       (any finite non-zero vector; normalized) */
 } vrt_render_params;
 
 typedef struct {
@@ -174,9 +186,13 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
  * voxel holding segments has that voxel listed and is traced again, so the
  * image never depends on culling. Outputs are DEVICE buffers of width*height
  * entries, row-major from the top row: rgba_out float4 premultiplied (colour =
- * |unit tangent| * AO, alpha = 1 - transmittance), first_id_out the nearest
- * accepted segment id or -1 (nullable), first_t_out its depth or +inf
- * (nullable). Needs vrt_cull (and vrt_build_mips when p->ao_cones > 0). */
+ * |unit tangent| * shading, alpha = 1 - transmittance; shading = per-hit AO,
+ * the voxel-space shading field or 1), first_id_out the nearest accepted
+ * segment id or -1 (nullable), first_t_out its depth or +inf (nullable).
+ * Needs vrt_cull (and vrt_build_mips when p->ao_cones > 0 or
+ * p->voxel_shading). With p->voxel_shading the call first computes the
+ * shading field (stage 8), and each repair round extends it next to the
+ * voxels it lists. */
 vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p,
                      float* rgba_out, int32_t* first_id_out, float* first_t_out);
 
@@ -201,6 +217,12 @@ vrt_status vrt_read_lists(vrt_grid g, uint32_t* start_host, uint32_t* len_host, 
 /* Test readback (waits): all pyramid levels, level 0 first, each canonical. */
 vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
 
+/* Test readback (waits): the voxel-space shading field of the last trace with
+ * p->voxel_shading, canonical order (n^3 floats); valid_host (nullable, n^3
+ * bytes) is 1 where the value was computed for that trace, and values_host
+ * is 0 elsewhere. VRT_ERR_STATE if no trace has used voxel shading. */
+vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host);
+
 /* Options. VRT_OPT_FORCE_EXACT (1): value 1 decides every list membership on
  * the exact integer path instead of the fp32 filter (for testing).
  * VRT_OPT_STAGE_TIMING (2): value 1 records CUDA events on the grid's stream
@@ -212,12 +234,17 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats);
  * from its stored children and rounded to nearest once, and the trace widens
  * the samples to fp32. Changing it invalidates the pyramid (vrt_build_mips
  * again). vrt_read_mips returns the stored values widened to fp32.
- * VRT_OPT_GRAPH (5): value 1 makes vrt_frame run as a CUDA graph (see there). */
+ * VRT_OPT_GRAPH (5): value 1 makes vrt_frame run as a CUDA graph (see there).
+ * VRT_OPT_CULL_DEPTH (6): value v > 0 culls a voxel once the estimated
+ * optical depth in front of it exceeds v / 1000 instead of ln(1e4) + 3; 0
+ * restores the default. For testing: a small threshold culls voxels that rays
+ * reach, which the repair rounds then list; the image does not change. */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
 #define VRT_OPT_TRACE_COUNTERS 3
 #define VRT_OPT_MIPS_FORMAT 4
 #define VRT_OPT_GRAPH 5
+#define VRT_OPT_CULL_DEPTH 6
 #define VRT_MIPS_F32 0
 #define VRT_MIPS_F16 1
 #define VRT_MIPS_BF16 2
@@ -263,9 +290,10 @@ vrt_status vrt_set_stream(vrt_grid g, void* cuda_stream);
 /* Stage durations of the last frame in milliseconds (waits), measured with
  * CUDA events on the grid's stream while VRT_OPT_STAGE_TIMING is on. Order:
  * 0 ingest, 1 voxelize pass 1, 2 mips, 3 cull marks, 4 scan, 5 voxelize
- * pass 2, 6 trace, 7 repair rounds (list + re-trace). Stages that did not run
- * since the last vrt_voxelize read -1. Writes min(n, 8) entries. */
-#define VRT_N_STAGES 8
+ * pass 2, 6 trace, 7 repair rounds (list + re-trace), 8 voxel-space shading.
+ * Stages that did not run since the last vrt_voxelize read -1. Writes
+ * min(n, 9) entries. */
+#define VRT_N_STAGES 9
 vrt_status vrt_get_stage_ms(vrt_grid g, float* ms, int32_t n);
 
 /* Exclusive prefix sum of per-voxel counts that allocates no device memory.

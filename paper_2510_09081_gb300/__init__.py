@@ -26,13 +26,14 @@ OPT_STAGE_TIMING = 2
 OPT_TRACE_COUNTERS = 3
 OPT_MIPS_FORMAT = 4
 OPT_GRAPH = 5
+OPT_CULL_DEPTH = 6
 MIPS_F32, MIPS_F16, MIPS_BF16 = 0, 1, 2
-STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair"]
+STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair", "shade"]
 
 # Exported symbols of the C ABI (include/vrt.h)
 SYMBOLS = ["vrt_create_grid", "vrt_upload_segments", "vrt_update_vertices", "vrt_voxelize",
            "vrt_build_mips", "vrt_cull", "vrt_trace", "vrt_sync", "vrt_get_stats",
-           "vrt_read_grid", "vrt_read_lists", "vrt_read_mips", "vrt_set_option",
+           "vrt_read_grid", "vrt_read_lists", "vrt_read_mips", "vrt_read_shading", "vrt_set_option",
            "vrt_get_stage_ms", "vrt_scan_counts_noalloc", "vrt_last_error", "vrt_destroy",
            "vrt_grid_device_bytes", "vrt_set_stream", "vrt_server_create", "vrt_server_add_set",
            "vrt_server_submit", "vrt_server_poll", "vrt_server_get_stats", "vrt_server_destroy",
@@ -77,7 +78,7 @@ class CameraC(ctypes.Structure):
 
 class RenderParamsC(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("ao_cones", ctypes.c_int32), ("cull", ctypes.c_int32),
-                ("k", ctypes.c_int32)]
+                ("k", ctypes.c_int32), ("voxel_shading", ctypes.c_int32), ("light", ctypes.c_float * 3)]
 
 
 class StatsC(ctypes.Structure):
@@ -114,6 +115,7 @@ def load():
         "vrt_read_grid": [P, P],
         "vrt_read_lists": [P, P, P, P, u64, ctypes.POINTER(u64)],
         "vrt_read_mips": [P, P, u64],
+        "vrt_read_shading": [P, P, P],
         "vrt_set_option": [P, i32, i64],
         "vrt_get_stage_ms": [P, P, i32],
         "vrt_scan_counts_noalloc": [P, P, P, u64, P, P, P],
@@ -181,8 +183,11 @@ def camera_c(cam) -> CameraC:
     return c
 
 
-def params_c(alpha=1.0, ao_cones=0, cull=0, k=0) -> RenderParamsC:
-    return RenderParamsC(alpha=float(alpha), ao_cones=int(ao_cones), cull=int(cull), k=int(k))
+def params_c(alpha=1.0, ao_cones=0, cull=0, k=0, voxel_shading=0, light=(0.0, 0.0, 1.0)) -> RenderParamsC:
+    p = RenderParamsC(alpha=float(alpha), ao_cones=int(ao_cones), cull=int(cull), k=int(k),
+                      voxel_shading=int(voxel_shading))
+    p.light[:] = [float(v) for v in light]
+    return p
 
 
 # ------------------------------------------------------------ C entry points
@@ -267,6 +272,15 @@ def read_lists(g, n, cap=None):
     return start, ln, ids[:int(tot.value)]
 
 
+def read_shading(g, n):
+    """The voxel-space shading field of the last shaded trace, [z, y, x], and
+    the mask of voxels it computed."""
+    vals = np.zeros((n, n, n), np.float32)
+    valid = np.zeros((n, n, n), np.uint8)
+    _check(load().vrt_read_shading(g, vals.ctypes.data, valid.ctypes.data), g)
+    return vals, valid.astype(bool)
+
+
 def read_mips(g, n):
     sizes, m = [], n
     while m >= 1:
@@ -341,13 +355,14 @@ class Renderer:
                           torch.empty((height, width), dtype=torch.float32, device="cuda"))
         return self._bufs
 
-    def frame(self, cam, alpha=1.0, ao_cones=0, cull_on=0, k=0, voxelize_first=True):
-        p = params_c(alpha, ao_cones, cull_on, k)
+    def frame(self, cam, alpha=1.0, ao_cones=0, cull_on=0, k=0, voxelize_first=True,
+              voxel_shading=0, light=(0.0, 0.0, 1.0)):
+        p = params_c(alpha, ao_cones, cull_on, k, voxel_shading, light)
         c = camera_c(cam)
         rgba, fid, ft = self.buffers(c.width, c.height)
         if voxelize_first:
             voxelize(self.h)
-            if ao_cones:
+            if ao_cones or voxel_shading:
                 build_mips(self.h)
         cull(self.h, c, p)
         trace(self.h, c, p, rgba, fid, ft)
@@ -436,7 +451,7 @@ class Server:
 
 
 def frame(g, cam_c, params, rgba, first_id=None, first_t=None, first_vertex=0, update=None):
-    """vrt_frame: update (optional) + voxelize + mips (AO) + cull + trace."""
+    """vrt_frame: update (optional) + voxelize + mips (AO or voxel shading) + cull + trace."""
     if update is None:
         upd, n, stride, dev = None, 0, 3, 0
     else:

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvrt.so")
 SOURCES = ["api.cu", "ingest.cu", "voxelize.cu", "scan.cu", "mips.cu", "cull.cu", "trace.cu", "bricks.cu", "server.cu",
-           "scan_noalloc.cu"]
+           "scan_noalloc.cu", "shade.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -52,6 +52,9 @@ struct vrt_grid_s {
   uint32_t* pq[2] = {nullptr, nullptr};
   uint32_t pq_cap = 0;
   float4* resume = nullptr;  // [2 * pq_cap] ray state at the first culled voxel
+  float* shade = nullptr;         // [n^3] voxel-space shading field (brick order)
+  uint32_t* shade_mask = nullptr; // [n^3 / 32] voxels the last shaded trace computed
+  bool shade_valid = false;
   DevStatus* st = nullptr;
   int force_exact = 0;
   int trace_counters = 0;
@@ -71,6 +74,7 @@ struct vrt_grid_s {
   // vrt_frame as a CUDA graph: the executable graph (updated in place while
   // the frame's launch sequence keeps its shape) and the grid's own stream the
   // frame is captured on (the legacy default stream cannot be captured)
+  float cull_depth = 0.0f;  // VRT_OPT_CULL_DEPTH (0: the default threshold)
   bool use_graph = false;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -267,7 +271,8 @@ HostCamera host_cam(const vrt_camera* c) {
   return h;
 }
 
-enum { ST_INGEST, ST_PASS1, ST_MIPS, ST_CULL, ST_SCAN, ST_PASS2, ST_TRACE, ST_REPAIR };
+enum { ST_INGEST, ST_PASS1, ST_MIPS, ST_CULL, ST_SCAN, ST_PASS2, ST_TRACE, ST_REPAIR, ST_SHADE };
+static_assert(ST_SHADE + 1 == VRT_N_STAGES, "stage list");
 
 void stage_mark(vrt_grid g, int stage, int end) {
   if (!g->timing) return;
@@ -313,6 +318,7 @@ void free_all(vrt_grid g) {
   dfree(g, g->xq); dfree(g, g->rec);
   dfree(g, g->mips); dfree(g, g->vq[0]); dfree(g, g->vq[1]); dfree(g, g->pq[0]); dfree(g, g->pq[1]);
   dfree(g, g->resume);
+  dfree(g, g->shade); dfree(g, g->shade_mask);
   dfree(g, g->st);
 }
 
@@ -549,7 +555,7 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
     if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
     if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
     g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->btmp, g->cdist, g->emean,
-                               g->stream);
+                               g->cull_depth, g->stream);
   } else {
     VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
   }
@@ -578,6 +584,17 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
     return fail(g, VRT_ERR_INVALID_ARG, "k must be 0, 1, 8, 16 or 32");
   if (g->stage < 3) return fail(g, VRT_ERR_STATE, "vrt_cull first");
   if (p->ao_cones && !g->mips_valid) return fail(g, VRT_ERR_STATE, "vrt_build_mips first (ambient occlusion)");
+  if (p->voxel_shading != 0 && p->voxel_shading != 1)
+    return fail(g, VRT_ERR_INVALID_ARG, "voxel_shading must be 0 or 1");
+  double light[3] = {0.0, 0.0, 0.0};
+  if (p->voxel_shading) {
+    const double l2 = (double)p->light[0] * p->light[0] + (double)p->light[1] * p->light[1] +
+                      (double)p->light[2] * p->light[2];
+    if (!(l2 > 0.0) || !std::isfinite(l2))
+      return fail(g, VRT_ERR_INVALID_ARG, "light must be a finite non-zero direction");
+    for (int k = 0; k < 3; ++k) light[k] = p->light[k] / std::sqrt(l2);
+    if (!g->mips_valid) return fail(g, VRT_ERR_STATE, "vrt_build_mips first (voxel shading)");
+  }
   int K;
   if (p->alpha >= 1.0f) {
     K = 1;
@@ -597,6 +614,26 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
     VRT_CUDA(g, dalloc(g, &g->resume, 2 * (size_t)npx));
     g->pq_cap = npx;
   }
+  const size_t nv = (size_t)g->n * g->n * g->n;
+  ShadeArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  if (p->voxel_shading) {
+    if (!g->shade) VRT_CUDA(g, dalloc(g, &g->shade, nv));
+    if (!g->shade_mask) VRT_CUDA(g, dalloc(g, &g->shade_mask, nv / 32));
+    sa.g = gdev(g);
+    sa.mips = g->mips;
+    sa.mips_fmt = g->mips_fmt;
+    for (int l = 0; l < 11; ++l) sa.lev_off[l] = g->lev_off[l];
+    sa.n_levels = g->n_levels;
+    sa.ao = p->ao_cones ? 1 : 0;
+    sa.lx = (float)light[0]; sa.ly = (float)light[1]; sa.lz = (float)light[2];
+    sa.shade = g->shade;
+    sa.mask = g->shade_mask;
+    stage_mark(g, ST_SHADE, 0);
+    g->launches += launch_shade(sa, g->stream);
+    stage_mark(g, ST_SHADE, 1);
+    g->shade_valid = true;
+  }
   TraceArgs a;
   std::memset(&a, 0, sizeof(a));
   a.g = gdev(g);
@@ -604,7 +641,8 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.pos = g->pos; a.nrm = g->nrm;
   a.n_vert = (uint32_t)g->V;
   a.count = g->trace_counters;
-  a.alpha = p->alpha; a.ao = p->ao_cones ? 1 : 0;
+  a.alpha = p->alpha; a.ao = p->voxel_shading ? 2 : (p->ao_cones ? 1 : 0);
+  a.shade = p->voxel_shading ? g->shade : nullptr;
   a.mips = g->mips;
   a.mips_fmt = g->mips_fmt;
   for (int l = 0; l < 11; ++l) a.lev_off[l] = g->lev_off[l];
@@ -638,6 +676,13 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
       const int ci = r & 1, nx = ci ^ 1;
       g->launches += launch_repair_alloc(d, g->vq[ci], &g->st->vq_cnt[ci], &g->st->pq_cnt[ci],
                                          g->vq_cap, g->stream);
+      if (p->voxel_shading) {
+        ShadeArgs sr = sa;
+        sr.vq = g->vq[ci];
+        sr.vq_cnt = &g->st->vq_cnt[ci];
+        sr.vq_cap = g->vq_cap;
+        g->launches += launch_shade_repair(sr, g->stream);
+      }
       g->launches += launch_scatter(d, 2, g->need, &g->st->vq_cnt[ci], g->stream);
       g->launches += launch_repair_clear(d, g->need, g->vq[ci], &g->st->vq_cnt[ci], g->vq_cap, nx, g->stream);
       TraceArgs b = a;
@@ -760,6 +805,28 @@ vrt_status vrt_read_mips(vrt_grid g, float* host, uint64_t n_floats) {
   return VRT_OK;
 }
 
+vrt_status vrt_read_shading(vrt_grid g, float* values, uint8_t* valid) {
+  if (!g || !values) return fail(g, VRT_ERR_INVALID_ARG, "NULL argument");
+  if (!g->shade_valid) return fail(g, VRT_ERR_STATE, "no trace has used voxel shading");
+  const int n = g->n;
+  const size_t nv = (size_t)n * n * n;
+  std::vector<float> v(nv);
+  std::vector<uint32_t> m(nv / 32);
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+  VRT_CUDA(g, cudaMemcpy(v.data(), g->shade, nv * 4, cudaMemcpyDeviceToHost));
+  VRT_CUDA(g, cudaMemcpy(m.data(), g->shade_mask, nv / 8, cudaMemcpyDeviceToHost));
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y)
+      for (int x = 0; x < n; ++x) {
+        const uint32_t i = brick_index(x, y, z, g->log2nb);
+        const size_t o = ((size_t)z * n + y) * n + x;
+        const bool ok = (m[i >> 5] >> (i & 31)) & 1u;
+        values[o] = ok ? v[i] : 0.0f;
+        if (valid) valid[o] = ok ? 1 : 0;
+      }
+  return VRT_OK;
+}
+
 vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const float* xyz,
                      int32_t stride, int32_t on_device, const vrt_camera* cam,
                      const vrt_render_params* p, float* rgba, int32_t* first_id, float* first_t) {
@@ -769,7 +836,7 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
     vrt_status r = VRT_OK;
     if (n_vertices > 0) r = vrt_update_vertices(g, first_vertex, n_vertices, xyz, stride, on_device);
     if (r == VRT_OK) r = vrt_voxelize(g);
-    if (r == VRT_OK && p->ao_cones) r = vrt_build_mips(g);
+    if (r == VRT_OK && (p->ao_cones || p->voxel_shading)) r = vrt_build_mips(g);
     if (r == VRT_OK) r = vrt_cull(g, cam, p);
     if (r == VRT_OK) r = vrt_trace(g, cam, p, rgba, first_id, first_t);
     return r;
@@ -786,7 +853,10 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
   // every buffer the chain sizes lazily exists before the capture (no
   // allocation may happen inside one)
   const size_t nv = (size_t)g->n * g->n * g->n;
-  if (p->ao_cones && !g->mips) VRT_CUDA(g, dalloc(g, (float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  if ((p->ao_cones || p->voxel_shading) && !g->mips)
+    VRT_CUDA(g, dalloc(g, (float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  if (p->voxel_shading && !g->shade) VRT_CUDA(g, dalloc(g, &g->shade, nv));
+  if (p->voxel_shading && !g->shade_mask) VRT_CUDA(g, dalloc(g, &g->shade_mask, nv / 32));
   if (p->cull) {
     if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
     if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
@@ -926,6 +996,11 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
   }
   if (option == VRT_OPT_TRACE_COUNTERS) {
     g->trace_counters = value ? 1 : 0;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_CULL_DEPTH) {
+    if (value < 0 || value > 1000000) return fail(g, VRT_ERR_INVALID_ARG, "cull depth must be in [0, 1e6]");
+    g->cull_depth = (float)((double)value / 1000.0);
     return VRT_OK;
   }
   if (option == VRT_OPT_GRAPH) {

@@ -77,6 +77,7 @@ struct CullCam {
   float3 rt, up;                  // orthographic: half extents along right / up
   float hw, hh, lr, ll, lt, lb;   // |n| * sqrt(3)/2 margins
   float kappa;                    // optical depth per unit length at full occupancy
+  float depth_max;                // estimated depth beyond which a voxel is culled
   int ortho;
 };
 
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
         if (counted) {
           const float e = (float)__ldg(&eroded[brick_index(px, py, pz, g.log2nb)]) * (1.0f / 255.0f);
           depth = fmaf(cc.kappa * e, fminf(te, tmax) - tcur, depth);
-          if (depth > kCullDepth) { visible = false; done = true; break; }
+          if (depth > cc.depth_max) { visible = false; done = true; break; }
         }
         counted = true;
         if (te >= tmax) { done = true; break; }
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
         const float tz = leave(sz, 4 * bz, 4 * bz + 4, c.z, iz);
         const float te = fminf(tx, fminf(ty, tz));
         depth = fmaf(cc.kappa * __ldg(&emean[bidx]), fminf(te, tmax) - tcur, depth);
-        if (depth > kCullDepth) { visible = false; break; }
+        if (depth > cc.depth_max) { visible = false; break; }
         if (te >= tmax) break;
         if (te == tx) bx += sx; else if (te == ty) by += sy; else bz += sz;
         if ((unsigned)bx >= (unsigned)nb || (unsigned)by >= (unsigned)nb || (unsigned)bz >= (unsigned)nb) break;
@@ -206,7 +207,7 @@ float3 tof(D3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 }  // namespace
 
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                uint8_t* btmp, uint8_t* cdist, float* emean, cudaStream_t s) {
+                uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, cudaStream_t s) {
   const D3 eye = {cam.eye[0], cam.eye[1], cam.eye[2]};
   const D3 tgt = {cam.target[0], cam.target[1], cam.target[2]};
   const D3 upw = {cam.up[0], cam.up[1], cam.up[2]};
@@ -217,6 +218,7 @@ int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* e
   const double h = 0.8660254037844386;
   CullCam cc;
   cc.ortho = cam.ortho;
+  cc.depth_max = depth_max > 0.0f ? depth_max : kCullDepth;
   // x 1/2: sampled PWAA occupancy integrates to about 4/3 of the tubes' true
   // volume, and the estimate must stay below the depth a ray really sees
   cc.kappa = (float)(0.5 * 2.0 / (3.14159265358979323846 * g.r) *

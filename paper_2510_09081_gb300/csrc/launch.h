@@ -28,7 +28,7 @@ struct TraceArgs {
   const float4* nrm;
   uint32_t n_vert;           // vertices; list entries must be < n_vert - 1
   float alpha;
-  int ao;
+  int ao;                    // per-hit shading: 0 none, 1 cone AO, 2 voxel-space field
   const void* mips;          // occupancy pyramid, texels in format mips_fmt
   int mips_fmt;              // kMipsF32, kMipsF16 or kMipsBF16
   long long lev_off[11];
@@ -50,7 +50,31 @@ struct TraceArgs {
                              // (C, T), (first id bits, first t, voxel index bits, entry t)
   uint32_t short_list;       // lists up to this length share the warp entry by entry
   int count;                 // accumulate trace work counters
+  const float* shade;        // voxel-space shading field [n^3] (brick order), or null
 };
+
+// Voxel-space shading (Sec. 3.4, Shading): per voxel, cone AO at its centre
+// times 1/2 + 1/2 * the transmittance of a ray toward the light through the
+// base occupancy level, for every voxel within one step (26-neighbourhood) of a
+// listed voxel -- the voxels whose centres a trilinear sample at a hit reads.
+struct ShadeArgs {
+  GridDev g;
+  const void* mips;          // occupancy pyramid (format mips_fmt)
+  int mips_fmt;
+  long long lev_off[11];
+  int n_levels;
+  int ao;                    // 1: include the cone AO
+  float lx, ly, lz;          // unit direction toward the light
+  float* shade;              // [n^3] shading value per voxel (brick order)
+  uint32_t* mask;            // [n^3 / 32] voxels whose value is current this frame
+  const uint32_t* vq;        // repair: voxels listed in this round
+  const uint32_t* vq_cnt;
+  uint32_t vq_cap;
+};
+// Every voxel next to a listed one (one block per brick); rewrites the mask.
+int launch_shade(const ShadeArgs& a, cudaStream_t s);
+// Voxels next to the voxels a repair round listed, not yet shaded this frame.
+int launch_shade_repair(const ShadeArgs& a, cudaStream_t s);
 
 int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,
                    DevStatus* st, cudaStream_t s);
@@ -72,9 +96,11 @@ int launch_finalize(const GridDev& g, cudaStream_t s);
 int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off, int n_levels,
                 cudaStream_t s);
 // Cull marks; btmp, cdist: one byte per brick (scratch; distance to a brick
-// with eroded occupancy); emean: one float per brick (mean eroded occupancy).
+// with eroded occupancy); emean: one float per brick (mean eroded occupancy);
+// depth_max: estimated optical depth past which a voxel is culled (<= 0: the
+// default, ln(1e4) + 3).
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                uint8_t* btmp, uint8_t* cdist, float* emean, cudaStream_t s);
+                uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, cudaStream_t s);
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
 // Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
 // them, then clear their `need` bits and the next round's queue counters.

@@ -232,7 +232,7 @@ vrt_status issue(vrt_server s, Slot& sl, Request& rq) {
     r = vrt_update_vertices(g, rq.first, rq.n, rq.upd, 3, 0);
   }
   if (r == VRT_OK) r = vrt_voxelize(g);
-  if (r == VRT_OK && rq.p.ao_cones) r = vrt_build_mips(g);
+  if (r == VRT_OK && (rq.p.ao_cones || rq.p.voxel_shading)) r = vrt_build_mips(g);
   if (r == VRT_OK) r = vrt_cull(g, &rq.cam, &rq.p);
   if (r == VRT_OK) r = vrt_trace(g, &rq.cam, &rq.p, rq.rgba, rq.first_id, rq.first_t);
   if (r == VRT_OK && cudaLaunchHostFunc(sl.stream, on_frame_done, &sl) != cudaSuccess)

@@ -27,10 +27,11 @@
 //    drop, beyond which it rescans the list -- shades up to 32 of them in
 //    parallel (one per lane), and accumulates them in key order,
 //    C += T alpha c, T *= 1 - alpha, until T < 1e-4 (ground-truth order).
-// Shading: colour = |unit tangent| per component times cone-traced ambient
-// occlusion when enabled (six cones over the occupancy pyramid; a cone's
-// occlusion is 1 - prod(1 - s_k) over its samples, so the samples of one hit
-// can be taken by different lanes).
+// Shading: colour = |unit tangent| per component times either cone-traced
+// ambient occlusion per hit when enabled (six cones over the occupancy
+// pyramid; a cone's occlusion is 1 - prod(1 - s_k) over its samples, so the
+// samples of one hit can be taken by different lanes), or one trilinear sample
+// of the voxel-space shading field at the hit (Sec. 3.4, built by shade.cu).
 //
 // Culling validation: a ray that reaches a voxel holding segments but no list
 // queues the voxel (deduplicated by a bitmap), marches on as if the voxel were
@@ -44,6 +45,7 @@
 #include <cuda_fp16.h>
 
 #include "launch.h"
+#include "pyramid.cuh"
 
 namespace vrt {
 
@@ -51,8 +53,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
 constexpr int kRayKeys = 32;              // transparent, shared entries: hit slots per ray (shared memory)
 constexpr int kTraceThreads = 128;
-constexpr float kConeTan = 1.1180340f;    // tan(half angle), cos(half angle) = 2/3
-constexpr int kConeSteps = 4;             // samples per cone: t = 1, 2.118, 4.486, 9.502 (<= 16)
 
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, uint32_t i) {
   return (bits[i >> 5] >> (i & 31)) & 1u;
@@ -72,19 +72,12 @@ __device__ __forceinline__ float3 shfl3(float3 v, int src) {
                      __shfl_sync(FULL, v.z, src));
 }
 
-// ------------------------------------------------ ambient occlusion (Sec 3.4)
-// Texel i of a pyramid level stored in format fmt, widened to fp32.
-__device__ __forceinline__ float texel(const void* lev, int fmt, int m, int x, int y, int z) {
-  if ((unsigned)x >= (unsigned)m || (unsigned)y >= (unsigned)m || (unsigned)z >= (unsigned)m)
-    return 0.0f;
-  const long long i = ((long long)z * m + y) * m + x;
-  if (fmt == kMipsF16) return __half2float(__ldg((const __half*)lev + i));
-  if (fmt == kMipsBF16) return __bfloat162float(__ldg((const __nv_bfloat16*)lev + i));
-  return __ldg((const float*)lev + i);
-}
-
-__device__ __forceinline__ float trilinear(const void* lev, int fmt, int m, float scale, float3 q) {
-  const float ux = q.x * scale - 0.5f, uy = q.y * scale - 0.5f, uz = q.z * scale - 0.5f;
+// The voxel-space shading field at P: trilinear over voxel centres, texel
+// coordinates clamped to the grid. A hit accepted in voxel v reads only v and
+// its neighbours, all of which the shading pass computed.
+__device__ __forceinline__ float shade_at(const TraceArgs& A, float3 P) {
+  const int n1 = A.g.n - 1;
+  const float ux = P.x - 0.5f, uy = P.y - 0.5f, uz = P.z - 0.5f;
   const float fx0 = floorf(ux), fy0 = floorf(uy), fz0 = floorf(uz);
   const int x = (int)fx0, y = (int)fy0, z = (int)fz0;
   const float fx = ux - fx0, fy = uy - fy0, fz = uz - fz0;
@@ -96,56 +89,15 @@ __device__ __forceinline__ float trilinear(const void* lev, int fmt, int m, floa
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
         const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-        acc = fmaf(w, texel(lev, fmt, m, x + dx, y + dy, z + dz), acc);
+        const int xi = min(max(x + dx, 0), n1), yi = min(max(y + dy, 0), n1), zi = min(max(z + dz, 0), n1);
+        acc = fmaf(w, __ldg(&A.shade[brick_index(xi, yi, zi, A.g.log2nb)]), acc);
       }
   return acc;
 }
 
-// One cone sample: cone c (axis c/2, sign by parity), step k; returns 1 - s.
-__device__ float cone_sample_clear(const TraceArgs& A, float3 P, int c, int k) {
-  float t = 1.0f;
-  for (int q = 0; q < k; ++q) t += 0.5f * fmaxf(1.0f, 2.0f * t * kConeTan);
-  if (t > 16.0f) return 1.0f;
-  const float dia = fmaxf(1.0f, 2.0f * t * kConeTan);
-  const int maxl = A.n_levels - 1;
-  const float lam = fminf(log2f(dia), (float)maxl);
-  const int l0 = (int)floorf(lam);
-  const float fl = lam - (float)l0;
-  const float sg = (c & 1) ? -1.0f : 1.0f;
-  float3 q = P;
-  const int ax = c >> 1;
-  if (ax == 0) q.x += sg * t; else if (ax == 1) q.y += sg * t; else q.z += sg * t;
-  const int tb = A.mips_fmt == kMipsF32 ? 4 : 2;  // bytes per texel
-  const char* base = (const char*)A.mips;
-  float s = trilinear(base + tb * A.lev_off[l0], A.mips_fmt, A.g.n >> l0, 1.0f / (float)(1 << l0), q);
-  if (fl > 0.0f && l0 + 1 <= maxl)
-    s = (1.0f - fl) * s + fl * trilinear(base + tb * A.lev_off[l0 + 1], A.mips_fmt, A.g.n >> (l0 + 1),
-                                         1.0f / (float)(2 << l0), q);
-  return 1.0f - s;
-}
-
-// AO at P by one lane: mean over cones of prod_k (1 - s_k).
-__device__ __noinline__ float ao_lane(const TraceArgs& A, float3 P) {
-  float sum = 0.0f;
-  for (int c = 0; c < 6; ++c) {
-    float p = 1.0f;
-    for (int k = 0; k < kConeSteps; ++k) p *= cone_sample_clear(A, P, c, k);
-    sum += p;
-  }
-  return sum * (1.0f / 6.0f);
-}
-
-// AO at P (same P in every lane) by the whole warp: lane 4c + k takes sample k
-// of cone c.
-__device__ __noinline__ float ao_warp(const TraceArgs& A, float3 P) {
-  const int lane = threadIdx.x & 31;
-  float v = lane < 6 * kConeSteps ? cone_sample_clear(A, P, lane / kConeSteps, lane % kConeSteps) : 1.0f;
-  v *= __shfl_xor_sync(FULL, v, 1);
-  v *= __shfl_xor_sync(FULL, v, 2);   // product over the cone's 4 samples
-  float s = (lane < 6 * kConeSteps && (lane & 3) == 0) ? v : 0.0f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-  return s * (1.0f / 6.0f);
+// Per-hit shading factor: A.ao = 1 cone AO at P, 2 the voxel-space field.
+__device__ __noinline__ float hit_shade(const TraceArgs& A, float3 P) {
+  return A.ao == 2 ? shade_at(A, P) : ao_lane(A, P);
 }
 
 __device__ __forceinline__ float3 tangent_colour(const TraceArgs& A, uint32_t id) {
@@ -401,7 +353,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
       const uint32_t id = (uint32_t)(best & 0xffffffffu);
       const float t = __uint_as_float((uint32_t)(best >> 32));
       float3 c = tangent_colour(A, id);
-      if (A.ao) c = ao_warp(A, o + t * d) * c;
+      if (A.ao) c = (A.ao == 2 ? shade_at(A, o + t * d) : ao_warp(A, o + t * d)) * c;
       if (lane == L) {
         R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
         R.T *= (1.0f - A.alpha);
@@ -470,7 +422,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
         const uint32_t id = (uint32_t)(mine & 0xffffffffu);
         tq = __uint_as_float((uint32_t)(mine >> 32));
         c = tangent_colour(A, id);
-        if (A.ao) c = ao_lane(A, o + tq * d) * c;
+        if (A.ao) c = hit_shade(A, o + tq * d) * c;
       }
       // accumulate in key order
       for (int q = 0; q < n_out; ++q) {
@@ -628,7 +580,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       const uint32_t id = (uint32_t)(best & 0xffffffffu);
       const float t = __uint_as_float((uint32_t)(best >> 32));
       float3 c = tangent_colour(A, id);
-      if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
+      if (A.ao) c = hit_shade(A, R.o + t * R.d) * c;
       R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
       R.T *= (1.0f - A.alpha);
       R.first_id = (int)id;
@@ -661,7 +613,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     const uint32_t id = (uint32_t)(kq & 0xffffffffu);
     const float t = __uint_as_float((uint32_t)(kq >> 32));
     float3 c = tangent_colour(A, id);
-    if (A.ao) c = ao_lane(A, R.o + t * R.d) * c;
+    if (A.ao) c = hit_shade(A, R.o + t * R.d) * c;
     const float w = R.T * A.alpha;
     R.C[0] = fmaf(w, c.x, R.C[0]);
     R.C[1] = fmaf(w, c.y, R.C[1]);

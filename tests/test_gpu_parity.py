@@ -1,6 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, on seeded
 synthetic line sets that span many bricks, tiles and a ragged image edge.
 Tolerances are stated in tests/parity.py."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -412,4 +414,189 @@ def test_overflow_is_detected():
     with pytest.raises(vrt.VrtError) as e:
         vrt.sync(r.h)
     assert e.value.status == vrt.ERR_OVERFLOW
+    r.close()
+
+
+# ------------------------------------------------ voxel-space shading (Sec. 3.4)
+LIGHT = (0.3, -0.5, 0.8)
+
+
+def _dilate(m):
+    """Voxels within one step (26-neighbourhood) of a set voxel."""
+    n = m.shape[0]
+    p = np.pad(m, 1)
+    out = np.zeros_like(m)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                out |= p[dz:dz + n, dy:dy + n, dx:dx + n]
+    return out
+
+
+def _shadow_spread(spread, x, y, z, light):
+    """Bound on how far the shadow transmittance from the centre of (x, y, z)
+    can move when the level-0 texels move within `spread` ([z, y, x]): each
+    sample is a convex combination of texels, so it moves by at most the
+    weighted spread of its texels, and a product of factors in [0, 1] by at
+    most the sum of its factors' moves."""
+    n = spread.shape[0]
+    L = np.asarray(light, np.float64) / np.linalg.norm(light)
+    P = np.array([x, y, z], np.float64) + 0.5
+    k = np.arange(1, int(np.sqrt(3.0) * (n + 1)) + 3, dtype=np.float64)[:, None]
+    q = P + k * L
+    inside = np.all((q >= -0.5) & (q <= n + 0.5), axis=1)
+    q = q[:np.argmin(inside) if not inside.all() else len(q)]  # the march ends at the first outside
+    u = q - 0.5
+    b = np.floor(u).astype(np.int64)
+    f = u - b
+    tot = 0.0
+    for d in itertools.product((0, 1), repeat=3):
+        c = b + np.array(d)
+        ok = np.all((c >= 0) & (c < n), axis=1)
+        w = np.prod(np.where(np.array(d)[None, :] == 1, f, 1.0 - f), axis=1)
+        cc = np.clip(c, 0, n - 1)
+        tot += float((w * ok * spread[cc[:, 2], cc[:, 1], cc[:, 0]]).sum())
+    return tot
+
+
+def test_voxel_shading_field_matches_oracle():
+    ls, cam = _abc_small()
+    n = ls.n
+    o = oracle.Oracle.from_lineset(ls)
+    L = o.lists()
+    # a near-tie occupancy code may come out one step either way in fp32
+    spread = ((L["occ_hi"].astype(np.float64) - L["occ_lo"]) / 32.0).reshape(n, n, n)
+    r = gpu_grid(ls)
+    fields = {}
+    for ao in (0, 6):
+        r.frame(cam, alpha=0.4, ao_cones=ao, cull_on=1, voxel_shading=1, light=LIGHT)
+        vrt.sync(r.h)
+        fields[ao] = vrt.read_shading(r.h, n)
+    start, ln, _ = vrt.read_lists(r.h, n)
+    st = vrt.get_stats(r.h)
+    r.close()
+    listed = (ln > 0).reshape(n, n, n)
+    assert listed.sum() < st["occupied_voxels"]  # the cull dropped voxels
+    for ao in (0, 6):
+        assert np.array_equal(fields[ao][1], _dilate(listed))
+    vals0, valid = fields[0]
+    vals6 = fields[6][0]
+    idx = np.argwhere(valid)
+    rng = np.random.default_rng(4)
+    pick = idx[rng.choice(idx.shape[0], min(400, idx.shape[0]), replace=False)]
+    worst, worst_ao, widened = 0.0, 0.0, 0
+    for z, y, x in pick:
+        # shadow only: 1/2 + S/2, within the early stop (5e-5), fp32 rounding
+        # and the near-tie bound
+        ref = o.voxel_shade(x, y, z, LIGHT, ao_cones=0)
+        b = 0.5 * _shadow_spread(spread, x, y, z, LIGHT)
+        widened += b > 0
+        err = abs(float(vals0[z, y, x]) - ref)
+        assert err <= 2e-4 + b, (x, y, z, float(vals0[z, y, x]), ref, b)
+        if b == 0:
+            worst = max(worst, err)
+        # with AO: the ratio is the cone AO at the voxel centre (tolerance of
+        # the per-hit AO images)
+        ao_ref = o.ao((x + 0.5, y + 0.5, z + 0.5))
+        e_ao = abs(float(vals6[z, y, x]) / float(vals0[z, y, x]) - ao_ref)
+        assert e_ao <= RGBA_TOL, (x, y, z, e_ao)
+        worst_ao = max(worst_ao, e_ao)
+    assert vals0[valid].min() < 0.6 and vals0[valid].max() > 0.99  # shadows and light both occur
+    ao_seen = vals6[valid] / vals0[valid]
+    assert ao_seen.min() < 0.3 and ao_seen.max() > 0.7  # AO is partial, neither 0 nor 1
+    print(f"voxel shading field: {len(pick)} voxels, shadow worst error {worst:.2e} where no "
+          f"near-tie code is read ({widened} with a widened bound), AO worst error {worst_ao:.2e}")
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.4])
+def test_voxel_shading_images(alpha):
+    ls, cam = _abc_small()
+    o = oracle.Oracle.from_lineset(ls)
+    pix = np.random.default_rng(11).choice(cam.width * cam.height, 1500, replace=False)
+    ref = o.render_pixels(cam, pix, alpha=alpha, ao_cones=6, voxel_shading=1, light=LIGHT)
+    r = gpu_grid(ls)
+    rgba, fid, ft = gpu_image_vs(r, cam, alpha)
+    per_hit = gpu_image(r, cam, alpha=alpha, ao=6, cull=1)[0]
+    r.close()
+    res = compare_image(rgba.reshape(-1, 4)[pix], fid.reshape(-1)[pix], ft.reshape(-1)[pix], ref)
+    assert res["hits"] > 1000
+    assert_image(res, max_exempt_frac=0.02)
+    # the field (AO at voxel centres, and the shadow) is not the per-hit AO
+    assert np.abs(rgba - per_hit).max() > 0.05
+    ok = ((ref["exempt"] & 1) == 0) & (fid.reshape(-1)[pix] >= 0)
+    d = np.abs(rgba.reshape(-1, 4)[pix] - ref["rgba"]).max(1)[ok]
+    print(f"voxel shading alpha {alpha}: RGBA error vs fp64 oracle over {ok.sum()} hit pixels: "
+          f"mean {d.mean():.2e} max {d.max():.2e}")
+
+
+def gpu_image_vs(r, cam, alpha, light=LIGHT, cull=1, ao=6):
+    rgba, fid, ft = r.frame(cam, alpha=alpha, ao_cones=ao, cull_on=cull, voxel_shading=1, light=light)
+    vrt.sync(r.h)
+    return rgba.cpu().numpy().copy(), fid.cpu().numpy().copy(), ft.cpu().numpy().copy()
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.3])
+def test_voxel_shading_culling_never_changes_the_image(alpha):
+    # culling lists fewer voxels, so fewer get shaded; every voxel a hit
+    # samples is still computed (repair rounds extend the field), and with the
+    # same values, so the images are equal bitwise
+    ls = tiny_walks(n_lines=3000, n_verts=60, seed=9)
+    cam = _persp_cam(w=211, h=117)
+    r = gpu_grid(ls)
+    off = gpu_image_vs(r, cam, alpha, light=(-0.2, 0.9, 0.4), cull=0, ao=6)
+    on = gpu_image_vs(r, cam, alpha, light=(-0.2, 0.9, 0.4), cull=1, ao=6)
+    # a much lower cull threshold: voxels rays reach are culled, listed and
+    # shaded by the repair rounds
+    vrt.set_option(r.h, vrt.OPT_CULL_DEPTH, 300)
+    rep = gpu_image_vs(r, cam, alpha, light=(-0.2, 0.9, 0.4), cull=1, ao=6)
+    st = vrt.get_stats(r.h)
+    r.close()
+    for a, b, c in zip(off, on, rep):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, c)
+    assert st["repaired_voxels"] > 100 and st["repair_rounds"] >= 1, st
+    print(f"repaired voxels {st['repaired_voxels']}, rounds {st['repair_rounds']}")
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.3])
+def test_aggressive_culling_is_repaired(alpha):
+    # repair with resume under a cull that drops voxels rays need: the image is
+    # that of no culling, bitwise
+    ls = tiny_walks(n_lines=3000, n_verts=60, seed=9)
+    cam = _persp_cam(w=211, h=117)
+    r = gpu_grid(ls)
+    off = gpu_image(r, cam, alpha=alpha, cull=0)
+    vrt.set_option(r.h, vrt.OPT_CULL_DEPTH, 300)
+    on = gpu_image(r, cam, alpha=alpha, cull=1)
+    st = vrt.get_stats(r.h)
+    r.close()
+    for a, b in zip(off, on):
+        assert np.array_equal(a, b)
+    assert st["repaired_voxels"] > 100 and st["retraced_pixels"] > 100, st
+    print(f"alpha {alpha}: repaired voxels {st['repaired_voxels']}, rounds {st['repair_rounds']}, "
+          f"re-traced pixels {st['retraced_pixels']}")
+
+
+def test_voxel_shading_argument_errors():
+    ls = tiny_walks(n_lines=50, n_verts=20, n=32, seed=2)
+    cam = _persp_cam(n=32, w=32, h=24)
+    r = gpu_grid(ls)
+    vrt.voxelize(r.h)
+    c = vrt.camera_c(cam)
+    rgba = torch.zeros((24, 32, 4), device="cuda")
+    vrt.cull(r.h, c, vrt.params_c(alpha=1.0))
+    with pytest.raises(vrt.VrtError) as e:  # the pyramid is needed
+        vrt.trace(r.h, c, vrt.params_c(alpha=1.0, voxel_shading=1), rgba)
+    assert e.value.status == vrt.ERR_STATE
+    vrt.build_mips(r.h)
+    for bad in (dict(voxel_shading=2), dict(voxel_shading=1, light=(0.0, 0.0, 0.0)),
+                dict(voxel_shading=1, light=(float("nan"), 0.0, 1.0))):
+        with pytest.raises(vrt.VrtError) as e:
+            vrt.trace(r.h, c, vrt.params_c(alpha=1.0, **bad), rgba)
+        assert e.value.status == vrt.ERR_INVALID_ARG
+    with pytest.raises(vrt.VrtError) as e:
+        vrt.read_shading(r.h, 32)
+    assert e.value.status == vrt.ERR_STATE
+    vrt.trace(r.h, c, vrt.params_c(alpha=1.0, voxel_shading=1), rgba)
+    vrt.sync(r.h)
     r.close()
