@@ -17,6 +17,7 @@ Prints ONE JSON line (rank 0). Under torchrun each rank renders its own replica
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -40,6 +41,14 @@ def log(*a):
 
 
 # ---------------------------------------------------------------- workloads
+def orbit(cam, deg):
+    """cam turned by deg about the vertical axis through its target."""
+    a = np.deg2rad(deg)
+    e = np.array(cam.eye, np.float64) - np.array(cam.target, np.float64)
+    e = np.array([e[0] * np.cos(a) - e[1] * np.sin(a), e[0] * np.sin(a) + e[1] * np.cos(a), e[2]])
+    return dataclasses.replace(cam, eye=tuple(float(v) for v in np.array(cam.target) + e))
+
+
 def make_workload(name, scale=1.0):
     from gen import linesets as G
     if name == "bundles":
@@ -268,8 +277,19 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     vrt.set_option(r.h, vrt.OPT_GRAPH, 0 if args.no_graph else 1)
+    static_cams = None
+    if args.static:
+        # lists (and the pyramid) built once, for every occupied voxel; each
+        # frame traces from a camera turned one more degree about the target
+        p.cull = 0
+        with torch.cuda.stream(stream):
+            vrt.frame(r.h, c, p, rgba, fid, ft)
+        static_cams = [vrt.camera_c(orbit(cam, d)) for d in range(360)]
 
     def frame(f, host=False):
+        if static_cams is not None:
+            vrt.trace(r.h, static_cams[f % 360], p, rgba, fid, ft)
+            return
         # one call per frame: update, voxelize, pyramid (AO only), cull, trace;
         # replayed as a CUDA graph unless --no-graph
         first, blk = (upd_host if host else upd_dev)[f % n_upd]
@@ -325,7 +345,7 @@ def run_ours(args, rank, world, local_rank):
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
         vrt.sync(r.h)
-    h2d = int(upd_host[0][1].numel() * 4)
+    h2d = 0 if args.static else int(upd_host[0][1].numel() * 4)
     d2h = int(rgba.numel() * 4)
 
     # ---- one instrumented frame (not timed): list entries the rays examine
@@ -347,6 +367,8 @@ def run_ours(args, rank, world, local_rank):
         r.close()
         return None
     stages = {k: statistics.mean(v) for k, v in stage_ms.items() if v}
+    if args.static:  # a static frame runs the trace alone (the field is reused)
+        stages = {k: v for k, v in stages.items() if k == "trace"}
     hbm, hbm_src = hbm_peak()
     px = cam.width * cam.height
     frame_B = sum(stage_bytes(k, ls.n, ls.n_vertices, st, px) for k in stages)
@@ -372,7 +394,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else "")
                    + (f" [occupancy pyramid in {args.mips}]" if args.mips != "fp32" else "")
                    + (f" [voxel-space shading: AO x shadow toward {SHADING_LIGHT}]"
-                      if args.shading == "voxel" else ""),
+                      if args.shading == "voxel" else "")
+                   + (" [static scene: lists built once for every occupied voxel; each frame "
+                      "traces only, the camera turned 1 degree per frame]" if args.static else ""),
                    "l2": "flushed between frames (512 MB write)",
                    "cuda_graph": not args.no_graph,
                    "segments": ls.n_segments, "grid": ls.n, "pixels": px,
@@ -532,6 +556,8 @@ def main():
                     help="issue the frame's launches one by one instead of replaying a CUDA graph")
     ap.add_argument("--mips", choices=("fp32", "fp16", "bf16"), default="fp32",
                     help="storage of the occupancy pyramid (AO workloads)")
+    ap.add_argument("--static", action="store_true",
+                    help="static scene: build the lists once, then time trace-only frames")
     ap.add_argument("--shading", choices=("hit", "voxel"), default="hit",
                     help="hit: the workload's per-hit shading; voxel: voxel-space shading field "
                          "(AO when the workload has it, and a directional shadow)")

@@ -191,8 +191,13 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
  * segment id or -1 (nullable), first_t_out its depth or +inf (nullable).
  * Needs vrt_cull (and vrt_build_mips when p->ao_cones > 0 or
  * p->voxel_shading). With p->voxel_shading the call first computes the
- * shading field (stage 8), and each repair round extends it next to the
- * voxels it lists. */
+ * shading field (stage 8) -- unless the last shaded trace computed it from the
+ * same list build, pyramid, light and AO setting (a static scene traced again
+ * from another camera) -- and each repair round extends it next to the voxels
+ * it lists. Tracing again without a new vrt_cull reuses the lists: a static
+ * scene needs only this call per frame (Sec. 4), with lists built for every
+ * occupied voxel (p->cull = 0) or, when culled, extended by the repair
+ * rounds for the new camera. */
 vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p,
                      float* rgba_out, int32_t* first_id_out, float* first_t_out);
 

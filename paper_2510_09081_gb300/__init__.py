@@ -368,6 +368,15 @@ class Renderer:
         trace(self.h, c, p, rgba, fid, ft)
         return rgba, fid, ft
 
+    def trace_only(self, cam, alpha=1.0, ao_cones=0, k=0, voxel_shading=0, light=(0.0, 0.0, 1.0)):
+        """A frame of a static scene: trace with the lists (and voxel-space
+        field) of the last build."""
+        p = params_c(alpha, ao_cones, 0, k, voxel_shading, light)
+        c = camera_c(cam)
+        rgba, fid, ft = self.buffers(c.width, c.height)
+        trace(self.h, c, p, rgba, fid, ft)
+        return rgba, fid, ft
+
 
 def grid_device_bytes(g) -> int:
     out = ctypes.c_uint64(0)

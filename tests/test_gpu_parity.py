@@ -600,3 +600,45 @@ def test_voxel_shading_argument_errors():
     vrt.trace(r.h, c, vrt.params_c(alpha=1.0, voxel_shading=1), rgba)
     vrt.sync(r.h)
     r.close()
+
+
+def _orbit(cam, deg):
+    """The camera turned by deg about the vertical axis through its target."""
+    a = np.deg2rad(deg)
+    e = np.array(cam.eye) - np.array(cam.target)
+    e = np.array([e[0] * np.cos(a) - e[1] * np.sin(a), e[0] * np.sin(a) + e[1] * np.cos(a), e[2]])
+    return Camera(width=cam.width, height=cam.height, ortho=cam.ortho,
+                  eye=tuple(map(float, np.array(cam.target) + e)), target=cam.target, up=cam.up,
+                  fovy_deg=cam.fovy_deg, ortho_h=cam.ortho_h)
+
+
+@pytest.mark.parametrize("voxel_shading", [0, 1])
+def test_static_scene_trace_only_frames(voxel_shading):
+    # a static set is voxelized and listed once; each later frame only traces
+    # (Sec. 4): from any camera the image equals a full frame's, and the
+    # voxel-space field is reused rather than recomputed
+    ls = tiny_walks(n_lines=1500, n_verts=60, seed=21)
+    cam0 = _persp_cam(w=160, h=96)
+    kw = dict(alpha=0.4, ao_cones=6, cull_on=0, voxel_shading=voxel_shading, light=LIGHT)
+    r = gpu_grid(ls)
+    r.frame(cam0, **kw)
+    vrt.sync(r.h)
+    got, launches = [], []
+    for deg in (0, 25, 70, 160):
+        l0 = vrt.get_stats(r.h)["kernel_launches"]
+        rgba, fid, ft = r.trace_only(_orbit(cam0, deg), alpha=0.4, ao_cones=6,
+                                     voxel_shading=voxel_shading, light=LIGHT)
+        vrt.sync(r.h)
+        launches.append(vrt.get_stats(r.h)["kernel_launches"] - l0)
+        got.append((rgba.cpu().numpy().copy(), fid.cpu().numpy().copy(), ft.cpu().numpy().copy()))
+    r.close()
+    for deg, g in zip((0, 25, 70, 160), got):
+        f = gpu_grid(ls)
+        ref = f.frame(_orbit(cam0, deg), **kw)
+        vrt.sync(f.h)
+        for a, b in zip(g, ref):
+            assert np.array_equal(a, b.cpu().numpy())
+        f.close()
+    assert not np.array_equal(got[0][0], got[2][0])
+    # one trace launch per frame: no list build, and the field is reused
+    assert launches == [1, 1, 1, 1], launches
