@@ -409,12 +409,13 @@ class Server:
         return int(sid.value)
 
     def submit(self, set_id, cam, rgba, alpha=1.0, ao_cones=0, cull_on=0, first_id=None,
-               first_t=None, first_vertex=0, update=None) -> int:
+               first_t=None, first_vertex=0, update=None, voxel_shading=0,
+               light=(0.0, 0.0, 1.0)) -> int:
         """rgba (and first_id / first_t) are device tensors that must stay alive
         until the request completes; update: host float32 [k, 3] for vertices
         first_vertex .. first_vertex + k - 1."""
         c = camera_c(cam)
-        p = params_c(alpha, ao_cones, cull_on, 0)
+        p = params_c(alpha, ao_cones, cull_on, 0, voxel_shading, light)
         if update is None:
             upd, n_upd, stride = None, 0, 3
         else:

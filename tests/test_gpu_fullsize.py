@@ -106,6 +106,46 @@ def test_fullsize_culling_never_changes_the_image(frame):
     assert st["repaired_voxels"] >= 0
 
 
+def _dilate(m):
+    n = m.shape[0]
+    p = np.pad(m, 1)
+    out = np.zeros_like(m)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                out |= p[dz:dz + n, dy:dy + n, dx:dx + n]
+    return out
+
+
+def test_fullsize_voxel_shading_properties(frame):
+    # voxel-space shading without AO: every hit's factor is 1/2 + S/2 in
+    # [1/2, 1], so against the unshaded frame the first hits, depths and
+    # alpha are unchanged and each colour channel lies in [C/2, C]; the field
+    # covers exactly the listed voxels' neighbourhoods; culling (with repair)
+    # leaves the shaded image unchanged, bitwise
+    ls, cam, r = frame["ls"], frame["cam"], frame["r"]
+    light = (0.4, 0.5, 0.77)
+    out = []
+    for cull in (1, 0):
+        rgba, fid, ft = r.frame(cam, alpha=0.3, cull_on=cull, voxel_shading=1, light=light)
+        vrt.sync(r.h)
+        out.append((rgba.cpu().numpy().reshape(-1, 4).copy(), fid.cpu().numpy().reshape(-1).copy(),
+                    ft.cpu().numpy().reshape(-1).copy()))
+        if cull == 1:
+            _, valid = vrt.read_shading(r.h, ls.n)
+            _, ln, _ = vrt.read_lists(r.h, ls.n)
+            assert np.array_equal(valid, _dilate((ln > 0).reshape(ls.n, ls.n, ls.n)))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    rgba, fid, ft = out[0]
+    assert np.array_equal(fid, frame["fid"]) and np.array_equal(ft, frame["ft"])
+    assert np.array_equal(rgba[:, 3], frame["rgba"][:, 3])
+    c0 = frame["rgba"][:, :3]
+    assert (rgba[:, :3] <= c0 + 1e-6).all() and (rgba[:, :3] >= 0.5 * c0 - 1e-6).all()
+    hit = fid >= 0
+    assert (rgba[hit, :3].sum(1) < 0.95 * c0[hit].sum(1)).mean() > 0.2  # shadows are seen
+
+
 # --------------------------------------------------------------------------
 # Unsteady-flow pathlines: 1M particles x 32 vertices (31M segments) in the ABC
 # flow, 512^3 grid, radius 0.25, 1920x1080 from inside the domain, opaque,
@@ -195,6 +235,25 @@ def test_abc_fullsize_ao_properties(abc_frame):
     assert (rgba_ao[:, :3] <= rgba[:, :3] + 1e-6).all() and (rgba_ao[:, :3] >= 0).all()
     # the occluded interior must darken a good share of the hits
     assert (rgba_ao[hit, :3].sum(1) < 0.95 * rgba[hit, :3].sum(1)).mean() > 0.2
+
+
+def test_abc_fullsize_voxel_shading_properties(abc_frame):
+    # opaque, six-cone AO at voxel centres times 1/2 + S/2: first hits and
+    # alpha as without shading, colour only darkened, and differently from
+    # the per-hit AO image
+    cam, r = abc_frame["cam"], abc_frame["r"]
+    rgba, fid, ft = r.frame(cam, alpha=1.0, ao_cones=6, cull_on=1, voxel_shading=1,
+                            light=(0.4, 0.5, 0.77))
+    vrt.sync(r.h)
+    rgba, fid, ft = (rgba.cpu().numpy().reshape(-1, 4), fid.cpu().numpy().reshape(-1),
+                     ft.cpu().numpy().reshape(-1))
+    p_rgba, p_fid, p_ft = abc_frame["plain"]
+    assert np.array_equal(fid, p_fid) and np.array_equal(ft, p_ft)
+    assert np.array_equal(rgba[:, 3], p_rgba[:, 3])
+    assert (rgba[:, :3] <= p_rgba[:, :3] + 1e-6).all() and (rgba[:, :3] >= 0).all()
+    hit = fid >= 0
+    assert (rgba[hit, :3].sum(1) < 0.95 * p_rgba[hit, :3].sum(1)).mean() > 0.2
+    assert np.abs(rgba - abc_frame["ao"][0]).max() > 0.05
 
 
 def test_abc_reduced_scale_ao_images():

@@ -45,7 +45,8 @@ def _requests(sets, n_req, seed):
                           ls.n - 1.0).astype(np.float32)
         reqs.append(dict(set=k, cam=_camera(rng, ls.n, w, h), alpha=float(rng.uniform(0.2, 1.0)),
                          ao=int(rng.uniform() < 0.3) * 6, cull=int(rng.uniform() < 0.5),
-                         first=first, update=upd))
+                         first=first, update=upd, vs=int(rng.uniform() < 0.3),
+                         light=tuple(float(v) for v in rng.normal(size=3))))
     return reqs
 
 
@@ -60,7 +61,8 @@ def _plain(sets, reqs):
         r = rs[q["set"]]
         if q["update"] is not None:
             r.update(q["first"], q["update"])
-        rgba, fid, ft = r.frame(q["cam"], alpha=q["alpha"], ao_cones=q["ao"], cull_on=q["cull"])
+        rgba, fid, ft = r.frame(q["cam"], alpha=q["alpha"], ao_cones=q["ao"], cull_on=q["cull"],
+                                voxel_shading=q["vs"], light=q["light"])
         vrt.sync(r.h)
         out.append((rgba.cpu().numpy().copy(), fid.cpu().numpy().copy(), ft.cpu().numpy().copy()))
     for r in rs:
@@ -79,7 +81,8 @@ def _served(sets, reqs, **kw):
              torch.zeros((c.height, c.width), device="cuda"))
         bufs.append(b)
         rid[srv.submit(ids[q["set"]], c, b[0], alpha=q["alpha"], ao_cones=q["ao"], cull_on=q["cull"],
-                       first_id=b[1], first_t=b[2], first_vertex=q["first"], update=q["update"])] = i
+                       first_id=b[1], first_t=b[2], first_vertex=q["first"], update=q["update"],
+                       voxel_shading=q["vs"], light=q["light"])] = i
     res = srv.poll(wait=True)
     stats = srv.stats()
     srv.close()
@@ -117,7 +120,8 @@ def test_served_frames_with_evictions_equal_frames_alone():
     for ls in sets:
         r = vrt.Renderer(ls.n, ls.radius)
         r.upload(ls.xyz, ls.offsets)
-        r.frame(_camera(np.random.default_rng(0), ls.n, 96, 70), alpha=0.5, ao_cones=6, cull_on=1)
+        r.frame(_camera(np.random.default_rng(0), ls.n, 96, 70), alpha=0.5, ao_cones=6, cull_on=1,
+                voxel_shading=1)
         vrt.sync(r.h)
         sizes.append(vrt.grid_device_bytes(r.h))
         r.close()
@@ -167,8 +171,8 @@ def test_graph_frames_equal_separate_calls():
             upd = torch.from_numpy(upd).cuda()
         elif upd is not None and len(got) % 3 == 1:
             upd = torch.from_numpy(upd).pin_memory()  # pageable numpy otherwise (runs uncaptured)
-        vrt.frame(r.h, c, vrt.params_c(q["alpha"], q["ao"], q["cull"]), rgba, fid, ft,
-                  first_vertex=q["first"], update=upd)
+        vrt.frame(r.h, c, vrt.params_c(q["alpha"], q["ao"], q["cull"], 0, q["vs"], q["light"]),
+                  rgba, fid, ft, first_vertex=q["first"], update=upd)
         vrt.sync(r.h)
         got.append((rgba.cpu().numpy(), fid.cpu().numpy(), ft.cpu().numpy()))
     r.close()
