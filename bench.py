@@ -163,7 +163,7 @@ TRACE_FLOPS_PER_ENTRY = 82        # FP32 operations of one capsule entry test
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 TRACE_SOURCES = ("paper_2510_09081_gb300/csrc/trace.cu", "paper_2510_09081_gb300/csrc/vrt_internal.cuh",
-                 "paper_2510_09081_gb300/csrc/launch.h")
+                 "paper_2510_09081_gb300/csrc/launch.h", "paper_2510_09081_gb300/csrc/pyramid.cuh")
 TRACE_PROFILE = os.path.join(ROOT, "profiles", "k_trace_tile_bundles_traffic.md")
 
 

@@ -455,10 +455,13 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
 }
 
 // The pending voxels of the warp's lanes with lists up to A.short_list
-// entries, processed together: their entries are numbered one after another
-// (lane by lane) and the warp takes 32 at a time, one (ray, entry) pair per
-// lane (two such rounds per step), so lanes with short lists do not wait for
-// the longest one. Pairs that pass the line-distance test are queued per warp
+// entries, processed together. Lanes whose rays wait in the same voxel form a
+// group (neighbouring rays of the tile usually do); the entries of the
+// groups' distinct lists are numbered one after another and the warp takes 32
+// at a time, one entry per lane (two such rounds per step), so short lists do
+// not wait for the longest one. A lane loads its entry (segment id and end
+// points) once and line-tests it against every ray of the entry's group in
+// turn. Pairs that pass the line-distance test are queued per warp
 // in shared memory and get the capsule test 32 at a time. A hit goes to its ray's slots in shared memory
 // (the nearest key for an opaque ray; up to kRayKeys keys of a transparent
 // ray, sorted and composited by the ray's own lane afterwards). A transparent
@@ -476,7 +479,16 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
   const unsigned lt = (1u << lane) - 1u;
   const bool take = R.pending && R.end - R.beg <= A.short_list;
   const uint32_t len = take ? R.end - R.beg : 0u;
-  uint32_t incl = len;
+  // group of lanes waiting in the same voxel (same list start); its lowest
+  // lane numbers the list's entries. Opaque rays mostly end in their first
+  // listed voxel, so their groups are small: each ray is its own group there.
+  unsigned gm = take ? 1u << lane : 0u;
+  if (!OPAQUE) {
+    const unsigned tm = __ballot_sync(FULL, take);
+    gm = __match_any_sync(FULL, take ? R.beg : 0xffffffffu) & (take ? tm : 0u);
+  }
+  const uint32_t glen = (take && __ffs(gm) - 1 == lane) ? len : 0u;
+  uint32_t incl = glen;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t v = __shfl_up_sync(FULL, incl, o);
@@ -491,7 +503,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
   if (OPAQUE) s_best[tid] = ~0ull;
   else s_cnt[tid] = 0u;
   __syncwarp();
-  const uint32_t first = R.beg - (incl - len);  // entry g of this lane is lists[first + g]
+  const uint32_t first = R.beg - (incl - glen);  // entry g of a group's list is lists[first + g]
   const float r2 = A.g.r * A.g.r;
   const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
   unsigned n_cap = 0;
@@ -538,12 +550,53 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       qn -= 32;
     }
   };
+  // line tests of a loaded entry against the rays in mask m, one per round
+  auto test_group = [&](unsigned m, uint32_t id, float4 p0, float4 p1) {
+    while (__any_sync(FULL, m)) {
+      bool pass = false;
+      int j = 0;
+      if (m) {
+        j = __ffs(m) - 1;
+        m &= m - 1;
+        const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
+        pass = lines_may_meet(f3(ro), f3(rd), f3(p0), f3(p1), rrm);
+      }
+      append(pass, id, j);
+    }
+  };
   // two independent (owner search, list load, vertex loads) chains per step:
-  // the loop is bound by their latency
-  for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+  // the loads' latency is paid once per entry, whatever its group's size
+  if (OPAQUE) {
+    for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+      const uint32_t ga = t0 + lane, gb = ga + 32;
+      const int ja = owner(ga), jb = owner(gb);
+      const uint32_t fa = __shfl_sync(FULL, first, ja), fb = __shfl_sync(FULL, first, jb);
+      const bool va = ga < total, vb = gb < total;
+      uint32_t ida = 0, idb = 0;
+      if (va) ida = __ldg(&A.g.lists[fa + ga]);
+      if (vb) idb = __ldg(&A.g.lists[fb + gb]);
+      const bool oka = va && ida + 1 < A.n_vert, okb = vb && idb + 1 < A.n_vert;
+      if ((va && !oka) || (vb && !okb)) set_err(A.g.st, kErrBounds);
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+      if (oka) { a0 = __ldg(&A.pos[ida]); a1 = __ldg(&A.pos[ida + 1]); }
+      if (okb) { b0 = __ldg(&A.pos[idb]); b1 = __ldg(&A.pos[idb + 1]); }
+      bool pa = false, pb = false;
+      if (oka) {
+        const float4 ro = s_ray[0][wb + ja], rd = s_ray[1][wb + ja];
+        pa = lines_may_meet(f3(ro), f3(rd), f3(a0), f3(a1), rrm);
+      }
+      if (okb) {
+        const float4 ro = s_ray[0][wb + jb], rd = s_ray[1][wb + jb];
+        pb = lines_may_meet(f3(ro), f3(rd), f3(b0), f3(b1), rrm);
+      }
+      append(pa, ida, ja);
+      append(pb, idb, jb);
+    }
+  } else for (uint32_t t0 = 0; t0 < total; t0 += 64) {
     const uint32_t ga = t0 + lane, gb = ga + 32;
     const int ja = owner(ga), jb = owner(gb);
     const uint32_t fa = __shfl_sync(FULL, first, ja), fb = __shfl_sync(FULL, first, jb);
+    const unsigned ma = __shfl_sync(FULL, gm, ja), mb = __shfl_sync(FULL, gm, jb);
     const bool va = ga < total, vb = gb < total;
     uint32_t ida = 0, idb = 0;
     if (va) ida = __ldg(&A.g.lists[fa + ga]);
@@ -553,17 +606,8 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
     if (oka) { a0 = __ldg(&A.pos[ida]); a1 = __ldg(&A.pos[ida + 1]); }
     if (okb) { b0 = __ldg(&A.pos[idb]); b1 = __ldg(&A.pos[idb + 1]); }
-    bool pa = false, pb = false;
-    if (oka) {
-      const float4 ro = s_ray[0][wb + ja], rd = s_ray[1][wb + ja];
-      pa = lines_may_meet(f3(ro), f3(rd), f3(a0), f3(a1), rrm);
-    }
-    if (okb) {
-      const float4 ro = s_ray[0][wb + jb], rd = s_ray[1][wb + jb];
-      pb = lines_may_meet(f3(ro), f3(rd), f3(b0), f3(b1), rrm);
-    }
-    append(pa, ida, ja);
-    append(pb, idb, jb);
+    test_group(oka ? ma : 0u, ida, a0, a1);
+    test_group(okb ? mb : 0u, idb, b0, b1);
   }
   __syncwarp();
   capsule_stage(qn);
