@@ -51,7 +51,7 @@ namespace vrt {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
-constexpr int kRayKeys = 32;              // transparent, shared entries: hit slots per ray (shared memory)
+constexpr int kRayKeys = 40;              // transparent, shared entries: hit slots per ray (40 KB of shared memory per block)
 constexpr int kTraceThreads = 128;
 
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, uint32_t i) {
