@@ -52,6 +52,7 @@ struct vrt_grid_s {
   uint32_t* pq[2] = {nullptr, nullptr};
   uint32_t pq_cap = 0;
   float4* resume = nullptr;  // [2 * pq_cap] ray state at the first culled voxel
+  uint32_t* order = nullptr;      // [V] pass-1 processing order of the vertices' segments
   float* shade = nullptr;         // [n^3] voxel-space shading field (brick order)
   uint32_t* shade_mask = nullptr; // [n^3 / 32] voxels the last shaded trace computed
   bool shade_valid = false;
@@ -213,6 +214,59 @@ vrt_status copy_vertices(vrt_grid g, long long first, long long V, const float* 
   return VRT_OK;
 }
 
+// Pass-1 processing order, fixed at upload (the topology does not change
+// after it): polylines sorted by the 16^3 cell of their middle vertex (a
+// counting sort on the 12-bit Morton code), each polyline's vertices kept
+// together. Neighbouring warps then voxelize nearby segments, so the
+// packed-word atomics of the blocks in flight cover a small part of the grid.
+// Used from a side of kOrderMinSide, where the packed words (512 MB at 512^3)
+// far exceed the L2 cache; below it the words stay in L2 and the input order
+// is as good. The order only affects speed: every segment is voxelized once.
+constexpr int kOrderMinSide = 512;
+
+vrt_status build_order(vrt_grid g, const int64_t* offsets, long long P) {
+  const long long V = g->V;
+  std::vector<uint32_t> mid, poly;
+  mid.reserve((size_t)P);
+  poly.reserve((size_t)P);
+  for (long long p = 0; p < P; ++p)
+    if (offsets[p + 1] > offsets[p]) {
+      mid.push_back((uint32_t)(offsets[p] + (offsets[p + 1] - offsets[p] - 1) / 2));
+      poly.push_back((uint32_t)p);
+    }
+  const uint32_t Pn = (uint32_t)mid.size();
+  std::vector<uint16_t> key(Pn);
+  if (Pn > 0) {
+    uint32_t* d_mid = nullptr;
+    uint16_t* d_key = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_mid, Pn * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_key, Pn * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mid, mid.data(), Pn * sizeof(uint32_t), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) {
+      launch_poly_keys(g->raw, d_mid, Pn, g->n, d_key, g->stream);
+      e = cudaMemcpyAsync(key.data(), d_key, Pn * sizeof(uint16_t), cudaMemcpyDeviceToHost, g->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cudaFree(d_mid);
+    cudaFree(d_key);
+    if (e != cudaSuccess) return cuda_fail(g, e, "pass-1 order keys");
+  }
+  std::vector<uint32_t> start(4097, 0);
+  for (uint32_t q = 0; q < Pn; ++q) ++start[key[q] + 1];
+  for (int b = 0; b < 4096; ++b) start[b + 1] += start[b];
+  std::vector<uint32_t> sorted(Pn);
+  for (uint32_t q = 0; q < Pn; ++q) sorted[start[key[q]]++] = poly[q];
+  std::vector<uint32_t> order((size_t)V);
+  size_t k = 0;
+  for (uint32_t q = 0; q < Pn; ++q)
+    for (int64_t v = offsets[sorted[q]]; v < offsets[sorted[q] + 1]; ++v) order[k++] = (uint32_t)v;
+  if ((long long)k != V) return fail(g, VRT_ERR_INVALID_ARG, "offsets do not cover the vertices");
+  VRT_CUDA(g, cudaMemcpyAsync(g->order, order.data(), (size_t)V * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                              g->stream));
+  VRT_CUDA(g, cudaStreamSynchronize(g->stream));  // order is a host temporary
+  return VRT_OK;
+}
+
 void make_camdev(const HostCamera& c, CamDev& cd) {
   auto sub = [](const double* a, const double* b, double* o) { for (int k = 0; k < 3; ++k) o[k] = a[k] - b[k]; };
   auto nrm = [](double* v) { double l = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); for (int k = 0; k < 3; ++k) v[k] /= l; };
@@ -316,7 +370,7 @@ void free_all(vrt_grid g) {
   for (int i = 0; i < VRT_N_STAGES; ++i)
     for (int j = 0; j < 2; ++j)
       if (g->ev[i][j]) { cudaEventDestroy(g->ev[i][j]); g->ev[i][j] = nullptr; }
-  dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm);
+  dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm); dfree(g, g->order);
   dfree(g, g->word); dfree(g, g->cur); dfree(g, g->vis); dfree(g, g->bdist); dfree(g, g->btmp);
   dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->cdist); dfree(g, g->emean); dfree(g, g->lists); dfree(g, g->tile_state);
   dfree(g, g->xq); dfree(g, g->rec);
@@ -413,10 +467,11 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
   const long long V = n_vertices;
   if (V > g->V_alloc) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-    dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm);
+    dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm); dfree(g, g->order);
     g->V_alloc = 0;
     VRT_CUDA(g, dalloc(g, &g->raw, 3 * (size_t)V + 6));
     VRT_CUDA(g, dalloc(g, &g->flags, (size_t)V));
+    if (g->n >= kOrderMinSide) VRT_CUDA(g, dalloc(g, &g->order, (size_t)V));
     VRT_CUDA(g, dalloc(g, &g->pos, (size_t)V + 1));
     VRT_CUDA(g, dalloc(g, &g->nrm, (size_t)V + 1));
     g->V_alloc = V;
@@ -472,6 +527,10 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
     VRT_CUDA(g, cudaMemcpyAsync(g->flags, fl.data(), (size_t)V, cudaMemcpyHostToDevice, g->stream));
     vrt_status s = copy_vertices(g, 0, V, xyz, stride, on_device);
     if (s != VRT_OK) return s;
+    if (g->order) {
+      s = build_order(g, offsets, n_polylines);
+      if (s != VRT_OK) return s;
+    }
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));  // fl is a host temporary
   }
   g->stage = 1;
@@ -509,7 +568,7 @@ vrt_status vrt_voxelize(vrt_grid g) {
   g->launches += launch_ingest(g->raw, g->flags, g->V, g->pos, g->nrm, g->st, g->stream);
   stage_mark(g, ST_INGEST, 1);
   stage_mark(g, ST_PASS1, 0);
-  g->launches += launch_pass1(g->pos, g->nrm, g->V, gdev(g), g->stream);
+  g->launches += launch_pass1(g->pos, g->nrm, g->order, g->V, gdev(g), g->stream);
   g->launches += launch_brick_dist(gdev(g), g->btmp, g->bdist, g->stream);
   stage_mark(g, ST_PASS1, 1);
   VRT_CUDA(g, cudaGetLastError());

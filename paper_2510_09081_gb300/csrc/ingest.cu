@@ -49,4 +49,29 @@ int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* p
   return 1;
 }
 
+// Spatial key of a polyline: the 12-bit Morton code of the 16^3 cell of the
+// grid holding vertex mid[p] (any coordinate outside the grid, or not finite,
+// is clamped into it; the key only orders work).
+__global__ void k_poly_keys(const float* __restrict__ raw, const uint32_t* __restrict__ mid,
+                            uint32_t P, float cells_per_voxel, uint16_t* __restrict__ key) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const uint32_t v = mid[p];
+  uint32_t k = 0;
+  for (int a = 0; a < 3; ++a) {
+    const float c = raw[3 * (size_t)v + a] * cells_per_voxel;
+    const uint32_t q = c >= 0.0f ? (uint32_t)fminf(c, 15.0f) : 0u;  // NaN -> 0
+#pragma unroll
+    for (int b = 0; b < 4; ++b) k |= ((q >> b) & 1u) << (3 * b + a);
+  }
+  key[p] = (uint16_t)k;
+}
+
+int launch_poly_keys(const float* raw, const uint32_t* mid, uint32_t P, int n, uint16_t* key,
+                     cudaStream_t s) {
+  if (P == 0) return 0;
+  k_poly_keys<<<(P + 255) / 256, 256, 0, s>>>(raw, mid, P, 16.0f / (float)n, key);
+  return 1;
+}
+
 }  // namespace vrt

@@ -78,8 +78,14 @@ int launch_shade_repair(const ShadeArgs& a, cudaStream_t s);
 
 int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,
                    DevStatus* st, cudaStream_t s);
-int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,
-                  cudaStream_t s);
+// Pass 1 over the segments in the order `order` (V vertex indices, each
+// polyline's vertices consecutive; a polyline's last vertex starts no
+// segment), or in index order when `order` is null.
+int launch_pass1(const float4* pos, const float4* nrm, const uint32_t* order, long long V,
+                 const GridDev& g, cudaStream_t s);
+// 12-bit spatial keys (Morton code of the 16^3 cell) of the vertices mid[0..P).
+int launch_poly_keys(const float* raw, const uint32_t* mid, uint32_t P, int n, uint16_t* key,
+                     cudaStream_t s);
 // Empty-brick distance field from the counts of pass 1 (tmp: one byte per brick).
 int launch_brick_dist(const GridDev& g, uint8_t* tmp, uint8_t* dist, cudaStream_t s);
 // The three distance passes from per-brick bytes in tmp (0 = occupied, else

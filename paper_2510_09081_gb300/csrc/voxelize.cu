@@ -252,11 +252,15 @@ __device__ __forceinline__ void flush_culled(const GridDev& g, unsigned long lon
 }
 
 __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
-                                               const float4* __restrict__ nrm, long long V,
+                                               const float4* __restrict__ nrm,
+                                               const uint32_t* __restrict__ order, long long V,
                                                GridDev g) {
   const int lane = threadIdx.x & 31;
   const long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-  const long long i = base + lane;
+  // slots in spatial order (nearby segments in the same and neighbouring
+  // warps keep the packed-word atomics within a smaller part of the grid)
+  const long long k = base + lane;
+  const long long i = k < V ? (order ? (long long)__ldg(&order[k]) : k) : V;
   Walk w;
   w.n = 0;
   float3 n0 = make_float3(0.f, 0.f, 0.f), n1 = n0;
@@ -278,9 +282,12 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   // every lane's walk, packed, read by the lanes that take its candidates
   __shared__ PackedWalk s_w[256];
   __shared__ float4 s_n[2][256];  // clip normals at v0 and v1
+  __shared__ uint32_t s_seg[256];  // segment id of each lane's walk
   unsigned long long* srec = s_rec[threadIdx.x >> 5];
   const int tid = threadIdx.x, wb = tid & ~31;
   int wcount = 0;  // records staged by this warp (uniform)
+  // segment id of lane j's walk
+  auto seg_of = [&](int j) { return order ? s_seg[wb + j] : (uint32_t)(base + j); };
   // The warp's candidates, segment after segment, are numbered 0..total-1;
   // lane l takes number t0 + l and finds its segment by a binary search over
   // the inclusive prefix of the candidate counts.
@@ -292,6 +299,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   }
   const uint32_t total = __shfl_sync(FULLW, incl, 31);
   if (w.n) {
+    if (order) s_seg[tid] = (uint32_t)i;
     s_w[tid] = pack_walk(w, en, incl - w.n);
     s_n[0][tid] = make_float4(n0.x, n0.y, n0.z, 0.0f);
     s_n[1][tid] = make_float4(n1.x, n1.y, n1.z, 0.0f);
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
                    clip & 2u, x, y, z, F, sq);
     }
     const unsigned am = __ballot_sync(FULLW, keep);
-    if (keep) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | (uint32_t)(base + j);
+    if (keep) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg_of(j);
     wcount += __popc(am);
     if (wcount > kWarpRecords - 32) {
       __syncwarp();
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
       p = s_w[wb + j];
       dec = seg_stage2_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
       if (dec < 0) {
-        queue_exact(g, (uint32_t)(base + j), x, y, z);
+        queue_exact(g, seg_of(j), x, y, z);
         ++ex;
       }
     }
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
       p = s_w[wb + j];
       if (decode_candidate(p, g.n, gq - __float_as_uint(p.w3.w), x, y, z)) {
         if (g.force_exact) {
-          queue_exact(g, (uint32_t)(base + j), x, y, z);
+          queue_exact(g, seg_of(j), x, y, z);
           ++ex;
         } else {
           dec = seg_stage1_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
@@ -462,11 +470,11 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
   if (lane == 0 && listed) atomicAdd(&g.st->listed, listed);
 }
 
-int launch_pass1(const float4* pos, const float4* nrm, long long V, const GridDev& g,
-                 cudaStream_t s) {
+int launch_pass1(const float4* pos, const float4* nrm, const uint32_t* order, long long V,
+                 const GridDev& g, cudaStream_t s) {
   if (V < 2) return 0;
   const int T = 256;
-  k_pass1<<<(unsigned)((V - 1 + T - 1) / T), T, 0, s>>>(pos, nrm, V, g);
+  k_pass1<<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
   k_exact1<<<152 * 4, T, 0, s>>>(pos, nrm, g);
   return 2;
 }
