@@ -959,6 +959,7 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
   g->stream = user;
   if (r != VRT_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
+    std::memset(g->shade_key, 0xff, sizeof(g->shade_key));  // the captured shading never ran
     if (r != VRT_OK) return r;
     return cuda_fail(g, e, "stream capture of the frame");
   }
@@ -973,7 +974,10 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
   cudaError_t ie = cudaSuccess;
   if (!g->graph_exec) ie = cudaGraphInstantiate(&g->graph_exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (ie != cudaSuccess) return cuda_fail(g, ie, "cudaGraphInstantiate");
+  if (ie != cudaSuccess) {
+    std::memset(g->shade_key, 0xff, sizeof(g->shade_key));
+    return cuda_fail(g, ie, "cudaGraphInstantiate");
+  }
   VRT_CUDA(g, cudaGraphLaunch(g->graph_exec, g->stream));
   return VRT_OK;
 }
