@@ -1,0 +1,62 @@
+"""The multi-GPU path of the benchmark is replicas only (one independent frame
+stream per rank, no data-path collective). Its host logic -- the maximum of
+the ranks' timings, the whole-job value, and the reference arm running on
+rank 0 alone -- runs here as world-size-2 gloo process groups on the CPU."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r measured (8 + r, 9 + 2r) ms per frame (device, end to end)
+        got = bench.max_over_ranks([8.0 + rank, 9.0 + 2 * rank], world, "cpu")
+        dist.barrier()
+        out.put((rank, got, bench.job_ms_per_frame(got[0], world)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_value_world_2():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, got, job in res:
+        assert got == [9.0, 11.0]  # the slowest rank's timings on every rank
+        assert job == 4.5          # two replicas: a frame every 9 / 2 ms
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    # under torchrun the other ranks exit 0 without work and print nothing
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
