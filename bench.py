@@ -417,6 +417,8 @@ def run_ours(args, rank, world, local_rank):
                    "p99_ms": round(srt[min(len(srt) - 1, int(0.99 * len(srt)))], 4),
                    "wall_s": round(wall, 3),
                    "value_definition": "mean device time per frame (max over ranks) / ranks"},
+        "throughput": {"segments_per_s": round(ls.n_segments * world / (mean_ms * 1e-3), 1),
+                       "pixels_per_s": round(px * world / (mean_ms * 1e-3), 1)},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "counters": {k: st[k] for k in ("fragments", "fragments_listed", "occupied_voxels",
                                         "visible_voxels", "repaired_voxels", "retraced_pixels",
