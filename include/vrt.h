@@ -147,8 +147,13 @@ vrt_status vrt_create_grid(const vrt_grid_desc* desc, void* cuda_stream, vrt_gri
  * on_device == 0, else device memory. `polyline_offsets`: HOST array of
  * n_polylines + 1 non-decreasing int64, first 0 and last n_vertices; polyline
  * p owns vertices [offsets[p], offsets[p+1]). Copies everything; (re)allocates
- * the vertex buffers and, when max_fragments was 0, the list capacity. Host
- * coordinates outside [-256, 768) or not finite give VRT_ERR_INVALID_ARG. */
+ * the vertex buffers and, when max_fragments was 0, the list capacity. On a
+ * grid of side 512 or more it also fixes the order in which voxelization takes
+ * the polylines (sorted by the coarse cell of their middle vertex; one small
+ * kernel and a host counting sort, 4 bytes per vertex on the device), which
+ * later vertex updates keep; the order affects speed only. Host coordinates
+ * outside [-256, 768) or not finite give VRT_ERR_INVALID_ARG. Waits for the
+ * copies before returning. */
 vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int64_t n_vertices,
                                const int64_t* polyline_offsets, int64_t n_polylines,
                                int32_t on_device);
