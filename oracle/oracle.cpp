@@ -15,7 +15,7 @@
 //   * lists      -- per-voxel segment lists: segment i (vertex i -> i+1, Sec. 3.3)
 //                   is listed in voxel v iff the closed distance between the
 //                   segment and v's closed box is <= the list radius
-//                   (capsule voxelization, Sec. 3.1, "conservative"). Decided
+//                   (conservative capsule voxelization, Sec. 3.1). Decided
 //                   exactly in integers. Lists are sorted by segment id.
 //   * occupancy  -- Alg. 3 (PWAA-clamped clipped-capsule SDF of Alg. 2) sampled
 //                   at the voxel centre, quantized per contribution and summed
@@ -24,7 +24,7 @@
 //   * render     -- every hit of every listed segment along each pixel ray, the
 //                   first entry into the capsule kept when the clip planes keep
 //                   it, sorted by (t, id) and composited front to back
-//                   ("ground-truth transparency", Sec. 3.5); optional cone-traced
+//                   (ground-truth transparency, Sec. 3.5); optional cone-traced
 //                   ambient occlusion per hit (Sec. 3.4 cones over the occupancy
 //                   pyramid), or voxel-space shading (Sec. 3.4): ambient
 //                   occlusion and a directional shadow evaluated at voxel

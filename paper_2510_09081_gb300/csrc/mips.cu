@@ -1,5 +1,5 @@
 // A2: the averaging occupancy pyramid used by cone-traced ambient occlusion
-// (Sec. 3.1 "averaging mipmap", Sec. 3.4 cones). Level 0 is
+// (an averaging mipmap, Sec. 3.1; sampled by the cones of Sec. 3.4). Level 0 is
 // min(1, occupancy code sum / occ_scale) per voxel, level l+1 the mean of the
 // 8 children; each level is stored x-fastest (canonical) so the trace's
 // trilinear samples are plain strided loads. Texels are fp32, fp16 or bf16.

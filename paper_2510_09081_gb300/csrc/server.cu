@@ -1,4 +1,4 @@
-// Serving: a request loop over resident line sets (vrt.h, "serving").
+// Serving: a request loop over resident line sets (the vrt_server_* calls of vrt.h).
 //
 // One scheduler thread owns the sets' grids and the stream slots. Submitting
 // threads only copy their request into pinned host memory and queue it. The
