@@ -55,3 +55,37 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
 
 def test_build_targets_sm103a_only():
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+STRUCTS = {"vrt_grid_desc": "GridDesc", "vrt_camera": "CameraC", "vrt_render_params": "RenderParamsC",
+           "vrt_stats": "StatsC", "vrt_server_desc": "ServerDesc", "vrt_server_result": "ServerResult",
+           "vrt_server_stats": "ServerStats"}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Size and every field offset of each struct the binding mirrors, as the
+    host compiler lays them out from include/vrt.h."""
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    lines = ['#include <cstddef>', '#include <cstdio>', '#include "vrt.h"', 'int main() {']
+    for cname, pyname in STRUCTS.items():
+        lines.append(f'  std::printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in getattr(vrt, pyname)._fields_:
+            lines.append(f'  std::printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.cpp"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cxx, "-std=c++17", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, pyname in STRUCTS.items():
+        py = getattr(vrt, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
