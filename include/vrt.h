@@ -248,13 +248,32 @@ vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host)
  * VRT_OPT_CULL_DEPTH (6): value v > 0 culls a voxel once the estimated
  * optical depth in front of it exceeds v / 1000 instead of ln(1e4) + 3; 0
  * restores the default. For testing: a small threshold culls voxels that rays
- * reach, which the repair rounds then list; the image does not change. */
+ * reach, which the repair rounds then list; the image does not change.
+ * VRT_OPT_TEST_SCAN_STALL (7), for testing the bounded waits: value t >= 0
+ * makes tile t of the list-offset scan (4096 voxels per tile) skip publishing
+ * its look-back state and lets every look-back wait give up after 1024 polls
+ * instead of about 4 million, so the waits of the tiles after it run out:
+ * vrt_sync then returns VRT_ERR_TIMEOUT and the lists of that build are
+ * wrong (every list access stays bounded). -1 restores the normal scan. With
+ * g == NULL it applies, process-wide, to vrt_scan_counts_noalloc (status bit
+ * 0). No wait is left unbounded in either case.
+ * VRT_OPT_TRACE_SHORT_LIST (8): value in [0, 1024] (default 1024): voxel lists
+ * up to this length share the warp entry by entry in the trace; longer ones
+ * take the whole-warp path (one list at a time). The image does not depend on
+ * it; for testing that path.
+ * VRT_OPT_TRACE_RAY_KEYS (9): value in [1, 40] (default 40): hit slots per
+ * transparent ray and voxel on the shared-entry path; a ray with more hits in
+ * one voxel takes the whole-warp path for it. The image does not depend on
+ * it; for testing. */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
 #define VRT_OPT_TRACE_COUNTERS 3
 #define VRT_OPT_MIPS_FORMAT 4
 #define VRT_OPT_GRAPH 5
 #define VRT_OPT_CULL_DEPTH 6
+#define VRT_OPT_TEST_SCAN_STALL 7
+#define VRT_OPT_TRACE_SHORT_LIST 8
+#define VRT_OPT_TRACE_RAY_KEYS 9
 #define VRT_MIPS_F32 0
 #define VRT_MIPS_F16 1
 #define VRT_MIPS_BF16 2
@@ -321,9 +340,12 @@ vrt_status vrt_get_stage_ms(vrt_grid g, float* ms, int32_t n);
  *               the counts of marked voxels in the order given.
  *   n_voxels:   a multiple of 4096, at most 134217728 (512^3); anything else
  *               returns VRT_ERR_INVALID_ARG before any device work.
- *   total_out:  DEVICE, one entry (nullable): the sum of the marked counts.
- *   status_out: DEVICE, one entry (nullable): bit 0 is set (never cleared
- *               here) if a bounded wait gave up; the offsets are then wrong.
+ *   total_out:  DEVICE, one entry (nullable): the sum of the marked counts
+ *               (its low 32 bits when it exceeds 2^32 - 1).
+ *   status_out: DEVICE, one entry (nullable), bits set (never cleared here):
+ *               bit 0 if a bounded wait gave up (the offsets are then wrong);
+ *               bit 1 if the total exceeds 2^32 - 1, so that the offsets
+ *               past that point wrapped (each is its prefix sum mod 2^32).
  * words and offsets must be 16-byte aligned. The grid's own list build
  * orders voxels in 4^3 bricks (brick index x-fastest, then 16 z + 4 y + x
  * inside the brick); pass words in that order to reproduce its offsets.
@@ -340,7 +362,10 @@ vrt_status vrt_scan_counts_noalloc(const uint32_t* words, const uint32_t* marks,
                                    void* cuda_stream);
 
 /* Message for the last error of `g` (or, when g is NULL, of the last failed
- * create or stand-alone call). Valid until the next call on the grid. */
+ * call without a grid -- create, vrt_scan_counts_noalloc, vrt_tune_grid_side,
+ * the vrt_server_* calls -- made by the calling host thread; each thread keeps
+ * its own). Valid until that thread's next such call, or the next call on the
+ * grid. */
 const char* vrt_last_error(vrt_grid g);
 
 /* Wait for the stream, free every device buffer and the handle. */

@@ -27,6 +27,10 @@ OPT_TRACE_COUNTERS = 3
 OPT_MIPS_FORMAT = 4
 OPT_GRAPH = 5
 OPT_CULL_DEPTH = 6
+OPT_TEST_SCAN_STALL = 7
+OPT_TRACE_SHORT_LIST = 8
+OPT_TRACE_RAY_KEYS = 9
+NOALLOC_GAVE_UP, NOALLOC_WRAPPED = 1, 2   # status bits of scan_counts_noalloc
 MIPS_F32, MIPS_F16, MIPS_BF16 = 0, 1, 2
 STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair", "shade"]
 
@@ -311,6 +315,16 @@ def scan_counts_noalloc(words, offsets, marks=None, total=None, status=None, str
     """Exclusive scan of packed-word counts without any device allocation
     (vrt_scan_counts_noalloc). All arguments are torch CUDA tensors."""
     n = int(words.numel()) if n_voxels is None else int(n_voxels)
+    # the C call cannot see the tensors' sizes: n must fit every buffer it touches
+    if n > words.numel() or n > offsets.numel():
+        raise VrtError(ERR_INVALID_ARG, f"n_voxels {n} exceeds words ({words.numel()}) "
+                                        f"or offsets ({offsets.numel()})")
+    if marks is not None and marks.numel() * 32 < n:
+        raise VrtError(ERR_INVALID_ARG, f"marks hold {marks.numel() * 32} bits, n_voxels is {n}")
+    for name, t in (("words", words), ("offsets", offsets), ("marks", marks), ("total", total),
+                    ("status", status)):
+        if t is not None and (t.element_size() != 4 or not t.is_contiguous() or not t.is_cuda):
+            raise VrtError(ERR_INVALID_ARG, f"{name} must be a contiguous 32-bit CUDA tensor")
     _check(load().vrt_scan_counts_noalloc(_ptr(words), _ptr(marks), _ptr(offsets), n,
                                           _ptr(total), _ptr(status), _stream_ptr(stream)))
 
@@ -410,12 +424,12 @@ class Server:
 
     def submit(self, set_id, cam, rgba, alpha=1.0, ao_cones=0, cull_on=0, first_id=None,
                first_t=None, first_vertex=0, update=None, voxel_shading=0,
-               light=(0.0, 0.0, 1.0)) -> int:
+               light=(0.0, 0.0, 1.0), k=0) -> int:
         """rgba (and first_id / first_t) are device tensors that must stay alive
         until the request completes; update: host float32 [k, 3] for vertices
         first_vertex .. first_vertex + k - 1."""
         c = camera_c(cam)
-        p = params_c(alpha, ao_cones, cull_on, 0, voxel_shading, light)
+        p = params_c(alpha, ao_cones, cull_on, k, voxel_shading, light)
         if update is None:
             upd, n_upd, stride = None, 0, 3
         else:

@@ -80,6 +80,9 @@ struct vrt_grid_s {
   // the frame's launch sequence keeps its shape) and the grid's own stream the
   // frame is captured on (the legacy default stream cannot be captured)
   float cull_depth = 0.0f;  // VRT_OPT_CULL_DEPTH (0: the default threshold)
+  int scan_stall = -1;      // VRT_OPT_TEST_SCAN_STALL (-1: off)
+  uint32_t short_list = kShortList;  // VRT_OPT_TRACE_SHORT_LIST
+  uint32_t ray_keys = kRayKeys;      // VRT_OPT_TRACE_RAY_KEYS
   bool use_graph = false;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -90,7 +93,9 @@ struct vrt_grid_s {
   uint64_t dev_bytes = 0;
 };
 
-std::string g_create_error;  // last error without a grid (creation, stand-alone calls)
+// Last error without a grid (creation, stand-alone and server calls), one per
+// host thread, so failing calls on different threads do not race on it.
+thread_local std::string g_create_error;
 
 namespace {
 
@@ -320,6 +325,27 @@ bool camera_ok(const vrt_camera* c) {
   if (c->ortho) return c->ortho_h > 0;
   return c->fovy_deg > 0 && c->fovy_deg < 180;
 }
+
+}  // namespace
+
+const char* vrt::frame_args_error(const vrt_camera* cam, const vrt_render_params* p) {
+  if (!p) return "params is NULL";
+  if (!camera_ok(cam)) return "bad camera";
+  if (!(p->alpha > 0.0f && p->alpha <= 1.0f)) return "alpha must be in (0, 1]";
+  if (p->ao_cones != 0 && p->ao_cones != 6) return "ao_cones must be 0 or 6";
+  if (p->cull < 0 || p->cull > 2) return "cull must be 0, 1 or 2";
+  if (p->k != 0 && p->k != 1 && p->k != 8 && p->k != 16 && p->k != 32)
+    return "k must be 0, 1, 8, 16 or 32";
+  if (p->voxel_shading != 0 && p->voxel_shading != 1) return "voxel_shading must be 0 or 1";
+  if (p->voxel_shading) {
+    const double l2 = (double)p->light[0] * p->light[0] + (double)p->light[1] * p->light[1] +
+                      (double)p->light[2] * p->light[2];
+    if (!(l2 > 0.0) || !std::isfinite(l2)) return "light must be a finite non-zero direction";
+  }
+  return nullptr;
+}
+
+namespace {
 
 HostCamera host_cam(const vrt_camera* c) {
   HostCamera h;
@@ -625,7 +651,8 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
   }
   stage_mark(g, ST_CULL, 1);
   stage_mark(g, ST_SCAN, 0);
-  g->launches += launch_scan(d, cull ? 0 : 1, g->tile_state, g->n_tiles, g->stream);
+  g->launches += launch_scan(d, cull ? 0 : 1, g->tile_state, g->n_tiles, g->scan_stall,
+                             g->scan_stall >= 0 ? kSpinLimitTest : 0, g->stream);
   g->launches += launch_finalize(d, g->stream);
   stage_mark(g, ST_SCAN, 1);
   stage_mark(g, ST_PASS2, 0);
@@ -737,7 +764,8 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, tr_next), 0,
                               sizeof(unsigned int) * (kMaxRepairRounds + 1), g->stream));
   a.work_next = &g->st->tr_next[0];
-  a.short_list = kShortList;
+  a.short_list = g->short_list;
+  a.ray_keys = g->ray_keys;
   stage_mark(g, ST_TRACE, 0);
   g->launches += launch_trace(a, K, g->stream);
   stage_mark(g, ST_TRACE, 1);
@@ -1065,7 +1093,27 @@ vrt_status vrt_set_stream(vrt_grid g, void* cuda_stream) {
 }
 
 vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
+  if (option == VRT_OPT_TEST_SCAN_STALL) {
+    if (value < -1 || value >= (1ll << 30)) return fail(g, VRT_ERR_INVALID_ARG, "stall tile must be in [-1, 2^30)");
+    if (!g) {
+      set_noalloc_scan_stall(value);
+      return VRT_OK;
+    }
+    g->scan_stall = (int)value;
+    return VRT_OK;
+  }
   if (!g) return fail(nullptr, VRT_ERR_INVALID_ARG, "grid is NULL");
+  if (option == VRT_OPT_TRACE_SHORT_LIST) {
+    if (value < 0 || value > (int64_t)kShortList)
+      return fail(g, VRT_ERR_INVALID_ARG, "short-list limit must be in [0, 1024]");
+    g->short_list = (uint32_t)value;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_TRACE_RAY_KEYS) {
+    if (value < 1 || value > kRayKeys) return fail(g, VRT_ERR_INVALID_ARG, "ray key slots must be in [1, 40]");
+    g->ray_keys = (uint32_t)value;
+    return VRT_OK;
+  }
   if (option == VRT_OPT_FORCE_EXACT) {
     g->force_exact = value ? 1 : 0;
     return g->V_alloc ? size_exact_queue(g) : VRT_OK;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "vrt.h"
 #include "vrt_internal.cuh"
 
 namespace vrt {
@@ -49,6 +50,7 @@ struct TraceArgs {
   float4* resume;            // [2 * pixels] state of a ray at its first culled voxel:
                              // (C, T), (first id bits, first t, voxel index bits, entry t)
   uint32_t short_list;       // lists up to this length share the warp entry by entry
+  uint32_t ray_keys;         // hit slots per transparent ray on that path (<= kRayKeys)
   int count;                 // accumulate trace work counters
   const float* shade;        // voxel-space shading field [n^3] (brick order), or null
 };
@@ -96,8 +98,10 @@ int launch_brick_dist_passes(int log2nb, uint8_t* tmp, uint8_t* dist, cudaStream
 // (skipped when *pending is 0).
 int launch_scatter(const GridDev& g, int mode, const uint32_t* need, const uint32_t* pending,
                    cudaStream_t s);
+// stall_tile >= 0 (testing): that tile never publishes its look-back state,
+// so the tiles after it give up their waits after spin_limit polls.
 int launch_scan(const GridDev& g, int all_visible, unsigned long long* tile_state, uint32_t n_tiles,
-                 cudaStream_t s);
+                int stall_tile, int spin_limit, cudaStream_t s);
 int launch_finalize(const GridDev& g, cudaStream_t s);
 int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off, int n_levels,
                 cudaStream_t s);
@@ -114,5 +118,17 @@ int launch_repair_alloc(const GridDev& g, const uint32_t* vq, const uint32_t* vq
                         const uint32_t* pq_cnt, uint32_t vq_cap, cudaStream_t s);
 int launch_repair_clear(const GridDev& g, uint32_t* need, const uint32_t* vq,
                          const uint32_t* vq_cnt, uint32_t vq_cap, int next, cudaStream_t s);
+
+// Host-side checks shared by the C ABI and the serving loop: nullptr when the
+// camera and render parameters are acceptable to vrt_cull and vrt_trace, else
+// what is wrong.
+const char* frame_args_error(const vrt_camera* cam, const vrt_render_params* p);
+
+// Testing hook of vrt_scan_counts_noalloc (vrt_set_option(NULL,
+// VRT_OPT_TEST_SCAN_STALL, tile)): tile >= 0 makes that look-back tile skip
+// its publish and shortens every wait; -1 restores the normal scan.
+void set_noalloc_scan_stall(long long tile);
+
+constexpr int kSpinLimitTest = 1 << 10;  // look-back polls while a test stalls a tile
 
 }  // namespace vrt

@@ -26,7 +26,8 @@ __device__ __forceinline__ unsigned long long load_state(const unsigned long lon
 
 __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visible,
                                                        unsigned long long* tile_state,
-                                                       uint32_t n_tiles) {
+                                                       uint32_t n_tiles, int stall_tile,
+                                                       int spin_limit) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_prefix;
@@ -79,13 +80,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
   }
   const uint32_t thread_excl = warp_off + incl - sum;
 
-  // decoupled look-back (warp 0)
+  // decoupled look-back (warp 0); a stalled tile (testing) publishes nothing,
+  // so the waits of the tiles after it run out
+  const bool publish = (int)tile != stall_tile;
   if (warp == 0) {
     uint32_t excl = 0;
     if (tile == 0) {
-      if (lane == 0) atomicExch(&tile_state[0], kFlagPrefix | agg);
+      if (lane == 0 && publish) atomicExch(&tile_state[0], kFlagPrefix | agg);
     } else {
-      if (lane == 0) atomicExch(&tile_state[tile], kFlagAgg | agg);
+      if (lane == 0 && publish) atomicExch(&tile_state[tile], kFlagAgg | agg);
       long long j = (long long)tile - 1;
       int spins = 0;
       bool done = false;
@@ -94,13 +97,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
         unsigned long long s = idx >= 0 ? load_state(&tile_state[idx]) : (kFlagPrefix | 0ull);
         // wait until every lane sees a published state
         while (__any_sync(0xffffffffu, (s >> 32) == 0)) {
-          if (++spins > kSpinLimit) break;
+          if (++spins > spin_limit) break;
           if ((s >> 32) == 0) {
             __nanosleep(64);
             s = load_state(&tile_state[idx]);
           }
         }
-        if (spins > kSpinLimit) {
+        if (spins > spin_limit) {
           if (lane == 0) set_err(g.st, kErrTimeout);
           break;
         }
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
         done = pmask != 0;
         j -= 32;
       }
-      if (lane == 0) atomicExch(&tile_state[tile], kFlagPrefix | (excl + agg));
+      if (lane == 0 && publish) atomicExch(&tile_state[tile], kFlagPrefix | (excl + agg));
     }
     if (lane == 0) {
       s_prefix = excl;
@@ -171,8 +174,9 @@ __global__ void k_finalize(GridDev g) {
 }
 
 int launch_scan(const GridDev& g, int all_visible, unsigned long long* tile_state, uint32_t n_tiles,
-                 cudaStream_t s) {
-  k_scan<<<n_tiles, kScanThreads, 0, s>>>(g, all_visible, tile_state, n_tiles);
+                int stall_tile, int spin_limit, cudaStream_t s) {
+  k_scan<<<n_tiles, kScanThreads, 0, s>>>(g, all_visible, tile_state, n_tiles, stall_tile,
+                                          spin_limit > 0 ? spin_limit : kSpinLimit);
   return 1;
 }
 

@@ -23,9 +23,10 @@
 
 #include <cuda_runtime.h>
 
+#include "launch.h"
 #include "vrt.h"
 
-extern std::string g_create_error;  // message returned by vrt_last_error(NULL)
+extern thread_local std::string g_create_error;  // message returned by vrt_last_error(NULL)
 
 namespace {
 
@@ -91,13 +92,13 @@ struct vrt_server_s {
   uint64_t tick = 0;
   int evictions = 0;
   int resident_sets = 0;
-  std::string err;
 };
 
 namespace {
 
-vrt_status sfail(vrt_server s, vrt_status st, const std::string& m) {
-  if (s) s->err = m;
+// Failures of server calls report through vrt_last_error(NULL), whose message
+// is kept per host thread.
+vrt_status sfail(vrt_server, vrt_status st, const std::string& m) {
   g_create_error = m;
   return st;
 }
@@ -318,7 +319,16 @@ void scheduler(vrt_server s) {
         r = issue(s, *free_slot, free_slot->req);
         lk.lock();
       }
-      if (r != VRT_OK) {  // failed before reaching the device
+      if (r != VRT_OK) {
+        // Part of the frame may already be on the slot's stream (the update
+        // copy from rq.upd, voxelization, ...): wait for it before the pinned
+        // buffer returns to the pool and the set can run on another slot.
+        if (ok) {
+          lk.unlock();
+          cudaStreamSynchronize(free_slot->stream);
+          vrt_sync(st.grid);  // drop a device status the partial frame may have left
+          lk.lock();
+        }
         st.busy = false;
         free_slot->busy = false;
         rq.t_issue = Clock::now();
@@ -406,6 +416,9 @@ vrt_status vrt_server_submit(vrt_server s, int32_t set_id, int64_t first_vertex,
   const Clock::time_point t0 = Clock::now();
   if (!s || !cam || !p || !rgba_out || !request_id) return sfail(s, VRT_ERR_INVALID_ARG, "NULL argument");
   if (stride != 3 && stride != 4) return sfail(s, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  // the checks vrt_cull and vrt_trace make, so that a bad request fails here
+  // and never reaches a stream
+  if (const char* why = vrt::frame_args_error(cam, p)) return sfail(s, VRT_ERR_INVALID_ARG, why);
   Request rq;
   {
     std::lock_guard<std::mutex> lk(s->mu);

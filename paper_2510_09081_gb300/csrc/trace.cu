@@ -52,7 +52,8 @@ namespace vrt {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
-constexpr int kRayKeys = 40;              // transparent, shared entries: hit slots per ray (40 KB of shared memory per block)
+// kRayKeys (vrt_internal.cuh): hit slots per transparent ray on the shared-entry
+// path, 40 KB of shared memory per block; A.ray_keys <= kRayKeys of them are used
 constexpr int kTraceThreads = 128;
 
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, uint32_t i) {
@@ -526,7 +527,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
           atomicMin(&s_best[wb + j], k);
         } else {
           const uint32_t slot = atomicAdd(&s_cnt[wb + j], 1u);
-          if (slot < (uint32_t)kRayKeys) s_key[slot * kTraceThreads + wb + j] = k;
+          if (slot < A.ray_keys) s_key[slot * kTraceThreads + wb + j] = k;
         }
       }
     }
@@ -637,7 +638,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     return;
   }
   const uint32_t nk = s_cnt[tid];
-  if (nk > (uint32_t)kRayKeys) return;  // stays pending: the whole-warp path redoes it
+  if (nk > A.ray_keys) return;  // stays pending: the whole-warp path redoes it
   if (COUNT) {
     ++R.n_vox;
     R.n_entries += len;

@@ -46,6 +46,46 @@ def test_host_side_argument_checks(lib):
     assert lib.vrt_destroy(None) == vrt.OK
 
 
+def test_option_and_message_checks_without_a_grid(lib):
+    """Options without a grid: only the no-allocation scan's test stall is
+    process-wide; everything else needs a grid. Messages are per host thread."""
+    import threading
+    assert lib.vrt_set_option(None, vrt.OPT_GRAPH, 1) == vrt.ERR_INVALID_ARG
+    assert lib.vrt_set_option(None, vrt.OPT_TEST_SCAN_STALL, -2) == vrt.ERR_INVALID_ARG
+    assert b"stall tile" in lib.vrt_last_error(None)
+    assert lib.vrt_set_option(None, vrt.OPT_TEST_SCAN_STALL, 7) == vrt.OK
+    assert lib.vrt_set_option(None, vrt.OPT_TEST_SCAN_STALL, -1) == vrt.OK
+    seen = {}
+
+    def other():
+        seen["before"] = lib.vrt_last_error(None)
+        lib.vrt_create_grid(None, None, ctypes.byref(ctypes.c_void_p()))
+        seen["after"] = lib.vrt_last_error(None)
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["before"] == b""            # a new thread starts with no message
+    assert seen["after"] != b"" and b"stall tile" in lib.vrt_last_error(None)
+
+
+def test_noalloc_binding_checks_sizes_before_the_call(lib):
+    """The C call cannot see tensor sizes: the binding refuses an n_voxels
+    beyond words, offsets or marks, and tensors that are not 32-bit CUDA ones."""
+    torch = pytest.importorskip("torch")
+    w = torch.zeros(4096, dtype=torch.int32)
+    for kw in (dict(n_voxels=8192), dict(marks=torch.zeros(64, dtype=torch.int32))):
+        with pytest.raises(vrt.VrtError) as e:
+            vrt.scan_counts_noalloc(w, torch.zeros(4096, dtype=torch.int32), **kw)
+        assert e.value.status == vrt.ERR_INVALID_ARG
+    with pytest.raises(vrt.VrtError, match="offsets"):
+        vrt.scan_counts_noalloc(w, torch.zeros(2048, dtype=torch.int32))
+    with pytest.raises(vrt.VrtError, match="CUDA tensor"):
+        vrt.scan_counts_noalloc(w, torch.zeros(4096, dtype=torch.int32))
+    with pytest.raises(vrt.VrtError, match="32-bit"):
+        vrt.scan_counts_noalloc(w, torch.zeros(4096, dtype=torch.int64))
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(vrt, "_lib", None)
     monkeypatch.setattr(vrt, "LIB_PATH", str(tmp_path / "missing.so"))

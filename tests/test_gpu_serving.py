@@ -7,8 +7,10 @@ again under a small HBM budget. Also the one-call frame as a CUDA graph
 import numpy as np
 import pytest
 
+import oracle
 import paper_2510_09081_gb300 as vrt
 from gen.linesets import Camera, tiny_walks
+from parity import compare_image
 
 pytestmark = pytest.mark.gpu
 
@@ -148,6 +150,70 @@ def test_server_errors():
     res = srv.poll(wait=True)
     assert len(res) == 1 and res[0]["status"] == vrt.ERR_OOM
     srv.close()
+
+
+def test_served_frames_match_the_oracle():
+    """Every frame of a served mix (updates, culling, AO, voxel-space shading,
+    several frames in flight) against the CPU oracle rendering the same set in
+    the state that request saw, within the parity tolerances."""
+    sets = _sets()[:3]
+    reqs = _requests(sets, 18, seed=11)
+    served, res, _ = _served(sets, reqs, max_inflight=3)
+    state = [ls.xyz.copy() for ls in sets]
+    n_hits = 0
+    for i, q in enumerate(reqs):
+        ls = sets[q["set"]]
+        if q["update"] is not None:
+            state[q["set"]][q["first"]:q["first"] + q["update"].shape[0]] = q["update"]
+        o = oracle.Oracle(state[q["set"]], ls.offsets, ls.n, ls.radius)
+        ref = o.render(q["cam"], alpha=q["alpha"], ao_cones=q["ao"], voxel_shading=q["vs"],
+                       light=q["light"])
+        o.close()
+        r = compare_image(*served[i], ref)
+        assert r["col_bad"] == 0 and r["id_bad"] == 0, (i, q["alpha"], q["ao"], q["vs"], r)
+        assert r["exempt_colour"] <= 0.01 * r["n"] and r["exempt_id"] <= 0.01 * r["n"], (i, r)
+        n_hits += r["hits"]
+    assert n_hits > 5000
+
+
+def test_bad_request_fails_at_submit_and_leaves_the_set_intact():
+    """A request whose camera or parameters vrt_cull / vrt_trace would reject
+    fails in vrt_server_submit, before any of its work (its vertex update
+    included) reaches the device; the set's next frames equal the frames
+    rendered alone."""
+    ls = _sets()[0]
+    rng = np.random.default_rng(4)
+    good = _requests([ls], 3, seed=12)
+    srv = vrt.Server(max_inflight=2)
+    sid = srv.add_set(ls.xyz, ls.offsets, ls.n, ls.radius)
+    cam = _camera(rng, ls.n, 48, 32)
+    rgba = torch.zeros((32, 48, 4), device="cuda")
+    upd = (ls.xyz[:50] + 0.25).astype(np.float32)
+    bad_kw = [dict(ao_cones=5), dict(alpha=0.0), dict(alpha=1.5), dict(cull_on=3), dict(k=7),
+              dict(voxel_shading=2), dict(voxel_shading=1, light=(0.0, 0.0, 0.0))]
+    for kw in bad_kw:
+        with pytest.raises(vrt.VrtError) as e:
+            srv.submit(sid, cam, rgba, first_vertex=0, update=upd, **kw)
+        assert e.value.status == vrt.ERR_INVALID_ARG, kw
+    bad_cam = Camera(width=48, height=32, ortho=0, eye=(1.0, 2.0, 3.0), target=(1.0, 2.0, 3.0),
+                     up=(0, 0, 1), fovy_deg=45.0)
+    with pytest.raises(vrt.VrtError) as e:
+        srv.submit(sid, bad_cam, rgba, first_vertex=0, update=upd)
+    assert e.value.status == vrt.ERR_INVALID_ARG
+    assert "camera" in str(e.value)
+    bufs = []
+    for q in good:
+        c = q["cam"]
+        b = torch.zeros((c.height, c.width, 4), device="cuda")
+        bufs.append(b)
+        srv.submit(sid, c, b, alpha=q["alpha"], ao_cones=q["ao"], cull_on=q["cull"],
+                   first_vertex=q["first"], update=q["update"], voxel_shading=q["vs"], light=q["light"])
+    res = srv.poll(wait=True)
+    srv.close()
+    assert [x["status"] for x in res] == [0] * len(good)
+    alone = _plain([ls], good)
+    for b, a in zip(bufs, alone):
+        assert np.array_equal(b.cpu().numpy(), a[0])
 
 
 def test_graph_frames_equal_separate_calls():

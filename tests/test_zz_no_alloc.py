@@ -75,12 +75,65 @@ def test_noalloc_scan_matches_the_list_build_twice(cull):
 
 
 def test_noalloc_scan_rejects_sizes_beyond_its_scratch():
+    """Sizes beyond the fixed scratch are rejected by the C entry point before
+    any device work (called through the C ABI directly, since the binding
+    would refuse these sizes first); sizes beyond the tensors by the binding."""
+    import ctypes
     words = torch.zeros(4096, dtype=torch.int32, device="cuda")
     offsets = torch.zeros(4096, dtype=torch.int32, device="cuda")
-    with pytest.raises(vrt.VrtError) as e:
-        vrt.scan_counts_noalloc(words, offsets, n_voxels=512 ** 3 + 4096)
-    assert e.value.status == vrt.ERR_INVALID_ARG
-    assert "scratch" in str(e.value)
-    with pytest.raises(vrt.VrtError) as e:
-        vrt.scan_counts_noalloc(words, offsets, n_voxels=4095)
-    assert e.value.status == vrt.ERR_INVALID_ARG
+    lib = vrt.load()
+    for n in (512 ** 3 + 4096, 4095, 0):
+        st = lib.vrt_scan_counts_noalloc(ctypes.c_void_p(words.data_ptr()), None,
+                                         ctypes.c_void_p(offsets.data_ptr()), n, None, None, None)
+        assert st == vrt.ERR_INVALID_ARG, n
+        if n > 512 ** 3:
+            assert b"scratch" in lib.vrt_last_error(None)
+    for kw in (dict(n_voxels=8192), dict(marks=torch.zeros(64, dtype=torch.int32, device="cuda"))):
+        with pytest.raises(vrt.VrtError) as e:
+            vrt.scan_counts_noalloc(words, offsets, **kw)
+        assert e.value.status == vrt.ERR_INVALID_ARG
+    with pytest.raises(vrt.VrtError):
+        vrt.scan_counts_noalloc(words, torch.zeros(2048, dtype=torch.int32, device="cuda"))
+
+
+def test_noalloc_scan_reports_a_total_past_32_bits():
+    """2^17 voxels of count 65535 sum to 8.6e9 > 2^32 - 1: status bit 1, and
+    each offset is its prefix sum modulo 2^32."""
+    n = 1 << 17
+    words = torch.full((n,), 0xFFFF, dtype=torch.int32, device="cuda")
+    offsets = torch.zeros(n, dtype=torch.int32, device="cuda")
+    total = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    vrt.scan_counts_noalloc(words, offsets, total=total, status=status)
+    torch.cuda.synchronize()
+    want = (np.arange(n, dtype=np.uint64) * 65535) % (1 << 32)
+    assert np.array_equal(offsets.cpu().numpy().view(np.uint32).astype(np.uint64), want)
+    assert int(total.cpu().numpy().view(np.uint32)[0]) == (n * 65535) % (1 << 32)
+    assert int(status.cpu()[0]) == vrt.NOALLOC_WRAPPED
+
+
+def test_noalloc_scan_wait_gives_up_then_scans_correctly_again():
+    """A test option makes tile 3 of 64 skip its publish: the waits after it
+    run out (after 1024 polls) and set status bit 0; with the option off, two
+    calls in a row give the right offsets again."""
+    n = 64 * 4096
+    rng = np.random.default_rng(3)
+    counts = rng.integers(0, 9, n).astype(np.uint32)
+    words = torch.from_numpy(counts.view(np.int32)).cuda()
+    want = np.concatenate([[0], np.cumsum(counts.astype(np.uint64))[:-1]])
+    offsets = torch.zeros(n, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    try:
+        vrt.set_option(None, vrt.OPT_TEST_SCAN_STALL, 3)
+        vrt.scan_counts_noalloc(words, offsets, status=status)
+        torch.cuda.synchronize()
+    finally:
+        vrt.set_option(None, vrt.OPT_TEST_SCAN_STALL, -1)
+    assert int(status.cpu()[0]) & vrt.NOALLOC_GAVE_UP
+    for call in range(2):
+        status.zero_()
+        offsets.fill_(-1)
+        vrt.scan_counts_noalloc(words, offsets, status=status)
+        torch.cuda.synchronize()
+        assert int(status.cpu()[0]) == 0, call
+        assert np.array_equal(offsets.cpu().numpy().view(np.uint32), want.astype(np.uint32)), call
