@@ -138,20 +138,26 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- roofline
-def stage_bytes(stage, n, V, st, px):
-    """Algorithmic (compulsory) DRAM bytes of one launch of a stage's kernels."""
+def stage_bytes(stage, n, V, st, px, tw=None, mips=False):
+    """Algorithmic (compulsory) DRAM bytes of one frame's stage: what the method
+    must move, not what the kernels happen to move. V vertices, n^3 voxels,
+    F_vis listed fragments, px pixels; the trace's share counts the distinct
+    list entries (4 B), vertices (16 B) and voxel words (8 B: packed word and
+    list end) its rays read, measured by the instrumented trace (tw)."""
     N3 = n ** 3
-    F, Fv = st["fragments"], st["fragments_listed"]
+    Fv = st["fragments_listed"]
+    tw = tw or {}
     return {
-        "ingest": 12 * V + V + 32 * V,                 # raw xyz + flags in, pos + clip normal out
-        "pass1": 32 * V + 4 * N3,                      # pos + normal in, packed words written back
-        "mips": 4 * N3 + 4 * N3 * 8 // 7,              # words in, pyramid out
-        "cull": 4 * N3 + N3 + N3 // 8,                 # words in, eroded + marks out
-        "scan": 4 * N3 + N3 // 8 + 4 * N3,             # words + marks in, offsets out
-        "pass2": 16 * V + 4 * Fv + 4 * N3,             # pos in, list entries + cursors out
-        "trace": 24 * px,                              # rgba + first id + first depth out
+        "ingest": 0,                                     # folded into pass 1's vertex read
+        "pass1": 16 * V + 8 * N3,                        # float4 vertices in; grid cleared + written back
+        "mips": (4 * N3 + 4 * N3 // 7) if mips else 0,   # level 0 in, levels >= 1 out
+        "cull": 4 * N3 + N3 // 7,                        # words in (with erosion halo), marks + OR pyramid out
+        "scan": 4 * N3 + 4 * N3,                         # counts in, offsets out
+        "pass2": 16 * V + 4 * Fv + 4 * N3,               # vertices in, list entries + cursors out
+        "trace": (24 * px + 4 * tw.get("unique_entries", 0) + 16 * tw.get("unique_vertices", 0)
+                  + 8 * tw.get("unique_voxels", 0)),     # outputs + what the rays read
         "repair": 0,
-        "shade": 4 * N3 + N3 // 8 + N3 // 8,           # words + marks read, field mask written
+        "shade": 4 * N3 + N3 // 8 + N3 // 8,             # words + marks read, field mask written
     }[stage]
 
 
@@ -233,11 +239,31 @@ def cpu_baseline(wl, budget_s=20.0):
             break
     t_render = time.perf_counter() - t0
     ms = 1e3 * (t_lists * step + t_render * npx / max(done, 1))
-    return {"value": ms, "unit": "ms/frame", "cores": cores, "kind": "oracle",
-            "sample": (f"lists of every {step}th polyline ({sub.n_segments} segments, x{step}) "
-                       f"+ render of {done} pixels of that sampled scene (x{npx / max(done, 1):.0f}); "
-                       "the sampled scene is sparser than the full one, so the render part is "
-                       "a lower bound")}
+    out = {"value": ms, "unit": "ms/frame", "cores": cores, "kind": "oracle",
+           "sample": (f"extrapolated from a bounded sample: the list build of every {step}th "
+                      f"polyline ({sub.n_segments} segments, timed, x{step}) plus the render of "
+                      f"{done} pixels (every {pstep}th row) of that sampled scene (timed, "
+                      f"x{npx / max(done, 1):.0f}); the sampled scene is sparser than the full "
+                      "one, so the render part is a lower bound")}
+    out["random_walks_full_frame"] = walks_full_frame(cores)
+    return out
+
+
+def walks_full_frame(cores):
+    """One whole frame of the random-walk workload (2000 x 50 vertices, 98k
+    segments, 64^3, 256x256 orthographic, opaque) on the oracle, measured end to
+    end: the list build from the raw vertices plus the render of every pixel."""
+    import oracle
+    from gen.linesets import tiny_walks, tiny_walks_camera
+    ls, cam = tiny_walks(), tiny_walks_camera()
+    t0 = time.perf_counter()
+    o = oracle.Oracle.from_lineset(ls, nthreads=cores)
+    o.build_lists()
+    o.render(cam, alpha=1.0)
+    ms = 1e3 * (time.perf_counter() - t0)
+    o.close()
+    return {"value": round(ms, 2), "unit": "ms/frame", "cores": cores, "segments": ls.n_segments,
+            "pixels": cam.width * cam.height, "measured": "one full frame, not extrapolated"}
 
 
 # ---------------------------------------------------------------- our arm
@@ -404,7 +430,20 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         frame(args.warmup)
         vrt.sync(r.h)
-    entries = vrt.get_stats(r.h)["trace_entries"]
+    stc = vrt.get_stats(r.h)
+    entries = stc["trace_entries"]
+    cyc = stc["trace_cycles"]
+    trace_work = {"entries": entries, "capsule_tests": stc["trace_capsule_tests"],
+                  "unique_entries": stc["trace_unique_entries"],
+                  "unique_vertices": stc["trace_unique_vertices"],
+                  "unique_voxels": stc["trace_unique_voxels"],
+                  "voxel_lists": stc["trace_voxels"], "dda_steps": stc["trace_steps"],
+                  "hits_found": stc["trace_hits"],
+                  "wholewarp_voxel_lists": stc["trace_wholewarp_voxels"],
+                  "wholewarp_entries": stc["trace_wholewarp_entries"],
+                  "cycle_share": {k: round(v / max(1, sum(cyc[:3])), 4) for k, v in
+                                  zip(("dda", "shared_entry", "whole_warp",
+                                       "capsule_tests_in_shared_entry"), cyc)}}
     vrt.set_option(r.h, vrt.OPT_TRACE_COUNTERS, 0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
@@ -419,7 +458,9 @@ def run_ours(args, rank, world, local_rank):
         stages = {k: v for k, v in stages.items() if k == "trace"}
     hbm, hbm_src = hbm_peak()
     px = cam.width * cam.height
-    frame_B = sum(stage_bytes(k, ls.n, ls.n_vertices, st, px) for k in stages)
+    frame_B = sum(stage_bytes(k, ls.n, ls.n_vertices, st, px, trace_work, mips=wl["ao"] > 0)
+                  for k in stages)
+    trace_B = stage_bytes("trace", ls.n, ls.n_vertices, st, px, trace_work)
     # dominant kernel: the trace (one launch per frame, timed by the library's
     # events on the grid's stream)
     alu_peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -458,6 +499,7 @@ def run_ours(args, rank, world, local_rank):
         "counters": {k: st[k] for k in ("fragments", "fragments_listed", "occupied_voxels",
                                         "visible_voxels", "repaired_voxels", "retraced_pixels",
                                         "exact_decisions", "max_count")},
+        "trace_work": trace_work,
         "roofline": {"bound": "alu", "kernel": "k_trace_tile (trace stage)",
                      "achieved": round(achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / alu_peak, 4),
@@ -466,7 +508,15 @@ def run_ours(args, rank, world, local_rank):
                      "work": (f"{entries} list entries examined x {TRACE_FLOPS_PER_ENTRY} FP32 ops "
                               "(one ray-capsule entry test each)"),
                      "traffic": trace_traffic(),
+                     "trace_algorithmic_bytes": trace_B,
+                     "trace_hbm_gbs": round(trace_B / (stages["trace"] * 1e-3) / 1e9, 1),
+                     "trace_hbm_frac": round(trace_B / (stages["trace"] * 1e-3) / 1e9 / hbm, 4),
                      "frame_algorithmic_bytes": frame_B,
+                     "frame_bytes_formula": ("16V + 8N^3 (pass 1) + [AO] 4N^3 + 4N^3/7 (pyramid) + "
+                                             "4N^3 + N^3/7 (cull) + 8N^3 (scan) + 16V + 4F_vis + 4N^3 "
+                                             "(pass 2) + 24 px + 4 F_t + 16 V_t + 8 N_t (trace: "
+                                             "distinct entries, vertices, voxels the rays read)"),
+                     "frame_hbm_gbs": round(frame_B / (mean_ms * 1e-3) / 1e9, 1),
                      "frame_hbm_frac": round(frame_B / (mean_ms * 1e-3) / 1e9 / hbm, 4),
                      "hbm_peak": hbm,
                      "hbm_peak_source": (f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"
@@ -481,6 +531,27 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
     r.close()
+    if args.workload == "bundles" and not args.no_serving and args.scale == 1.0 and not args.static:
+        # the metric's second half: served-frame latency over resident sets
+        del xyz_dev, flush
+        torch.cuda.empty_cache()
+        n_req = 40
+        sets, reqs, arrivals, total = serve_mix(n_req)
+        arms = serve_arms(sets, reqs, arrivals, local_rank)
+        out["serving"] = {
+            "workload": ("64 resident random-walk line sets, log-uniform 10k..5M segments (total "
+                         f"{total}), grids 128^3..512^3, outputs 720p..4K, alpha U[0.2, 1], 2% of "
+                         "vertices updated per request, automatic culling"),
+            "requests": n_req,
+            "served_frames_per_s": arms["served_capacity"]["frames_per_s"],
+            "plain_frames_per_s": arms["plain_capacity"]["frames_per_s"],
+            "p50_ms": arms["served_poisson"]["p50_ms"], "p99_ms": arms["served_poisson"]["p99_ms"],
+            "plain_p50_ms": arms["plain_poisson"]["p50_ms"],
+            "plain_p99_ms": arms["plain_poisson"]["p99_ms"],
+            "arms": arms,
+            "definition": ("served: 4 stream slots (frames of different sets overlap); plain: 1; "
+                           "frames/s with every request queued at once; latency submit -> frame "
+                           "finished seen by the host, Poisson arrivals at 200 requests/s")}
     if not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_baseline(wl)
@@ -493,16 +564,12 @@ def run_ours(args, rank, world, local_rank):
 SERVE_METRIC = "served frames/s over 64 resident line sets (Poisson 200 req/s); p50/p99 latency"
 
 
-def run_serve(args, rank):
-    """Frame requests over 64 resident random-walk line sets of log-uniform size
-    (10k..5M segments; grid 128^3 / 256^3 / 512^3 by size), each request a camera
-    (720p..4K), an opacity in [0.2, 1] and an update of 2% of the set's vertices.
-    Two loads: a Poisson stream at 200 requests/s (latency) and every request
-    queued at once (capacity); each with 4 stream slots (served) and with 1 (the
-    plain one-frame-at-a-time path)."""
-    if rank != 0:
-        return None
-    import torch
+def serve_mix(n_req):
+    """The serving workload: 64 resident random-walk line sets of log-uniform
+    size (10k..5M segments; grid 128^3 / 256^3 / 512^3 by size) and n_req frame
+    requests, each a camera (720p..4K), an opacity in [0.2, 1] and an update of
+    2% of the set's vertices, arriving as a Poisson stream at 200 requests/s."""
+    from gen import linesets as G
     import paper_2510_09081_gb300 as vrt
     from gen import linesets as G
     rng = np.random.default_rng(20251013)
@@ -515,7 +582,6 @@ def run_serve(args, rank):
         sets.append(G.walk_set(int(S), n, radius=0.4, seed=20251100 + 7 * k))
     log(f"[bench] {n_sets} sets, {int(sizes.sum())} segments, ready in {time.time() - t0:.1f}s")
     res_choices = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
-    n_req = max(args.steps, 40)
     arrivals = np.cumsum(rng.exponential(1.0 / 200.0, n_req))
     reqs = []
     for i in range(n_req):
@@ -532,7 +598,18 @@ def run_serve(args, rank):
         upd = np.clip(ls.xyz[first:first + cnt] + rng.normal(0, 0.05, (cnt, 3)), 1.0,
                       ls.n - 1.0).astype(np.float32)
         reqs.append((k, cam, float(rng.uniform(0.2, 1.0)), first, upd))
-    dev = torch.device("cuda", 0)
+    return sets, reqs, arrivals, int(sizes.sum())
+
+
+def serve_arms(sets, reqs, arrivals, device=0):
+    """Run the requests through the library's server: a Poisson stream at 200
+    requests/s (latency) and every request queued at once (capacity), each with
+    4 stream slots (served: frames of different sets overlap) and with 1 (the
+    plain one-frame-at-a-time path)."""
+    import torch
+    import paper_2510_09081_gb300 as vrt
+    n_sets = len(sets)
+    dev = torch.device("cuda", device)
     bufs = [torch.empty((2160, 3840, 4), dtype=torch.float32, device=dev) for _ in range(n_sets)]
 
     def arm(slots, paced):
@@ -561,6 +638,20 @@ def run_serve(args, rank):
 
     out = {"served_poisson": arm(4, True), "plain_poisson": arm(1, True),
            "served_capacity": arm(4, False), "plain_capacity": arm(1, False)}
+    del bufs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, rank):
+    """Serving (C4) as the benchmark's main line: frames/s with every request
+    queued at once, 4 stream slots; the other arms beside it."""
+    if rank != 0:
+        return None
+    n_req = max(args.steps, 40)
+    sets, reqs, arrivals, total = serve_mix(n_req)
+    out = serve_arms(sets, reqs, arrivals)
+    sizes_sum = total
     sp = out["served_capacity"]["frames_per_s"]
     return {"metric": SERVE_METRIC, "value": sp, "unit": "frames/s", "n_gpus": 1, "steps": n_req,
             "warmup": n_sets, "ms_per_step": round(1000.0 / sp, 4), "higher_is_better": True,
@@ -569,7 +660,7 @@ def run_serve(args, rank):
             "config": {"workload": ("serving: 64 resident random-walk line sets, log-uniform "
                                     "10k..5M segments (total %d), grids 128^3..512^3, outputs "
                                     "720p..4K, alpha U[0.2, 1], 2%% of vertices updated per "
-                                    "request, automatic culling" % int(sizes.sum())),
+                                    "request, automatic culling" % sizes_sum),
                        "value_definition": "frames/s with every request queued at once, 4 stream slots",
                        **out}}
 
@@ -601,11 +692,13 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave the serving leg out of the bundles line")
     ap.add_argument("--no-graph", action="store_true",
                     help="issue the frame's launches one by one instead of replaying a CUDA graph")
     ap.add_argument("--mips", choices=("fp32", "fp16", "bf16"), default="fp32",

@@ -134,6 +134,19 @@ typedef struct {
   uint64_t trace_capsule_tests; /* entries that passed the line-distance test */
   uint64_t trace_voxels;        /* voxel lists processed */
   uint64_t trace_steps;         /* DDA steps (voxels and empty bricks) */
+  uint64_t trace_wholewarp_voxels;  /* voxel lists taken by the whole-warp path */
+  uint64_t trace_wholewarp_entries; /* entries it examined, rescans included */
+  uint64_t trace_hits;              /* accepted hits handed to the rays */
+  uint64_t trace_cycles[4];         /* SM cycles summed over warps: DDA steps,
+                                       shared-entry path (with its compositing),
+                                       whole-warp path; [3]: the capsule tests
+                                       within the shared-entry path */
+  /* distinct list entries, vertices and voxels (their packed word and list
+     end) that the rays of the last instrumented vrt_trace read, repair rounds
+     included (0 unless VRT_OPT_TRACE_COUNTERS was on for it) */
+  uint64_t trace_unique_entries;
+  uint64_t trace_unique_vertices;
+  uint64_t trace_unique_voxels;
 } vrt_stats;
 
 /* Create a grid (Sec. 3.1). `cuda_stream` is a cudaStream_t (NULL = legacy

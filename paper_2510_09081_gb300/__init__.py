@@ -94,7 +94,10 @@ class StatsC(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("retraced_pixels", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("trace_entries", ctypes.c_uint64),
                 ("trace_capsule_tests", ctypes.c_uint64), ("trace_voxels", ctypes.c_uint64),
-                ("trace_steps", ctypes.c_uint64)]
+                ("trace_steps", ctypes.c_uint64), ("trace_wholewarp_voxels", ctypes.c_uint64),
+                ("trace_wholewarp_entries", ctypes.c_uint64), ("trace_hits", ctypes.c_uint64),
+                ("trace_cycles", ctypes.c_uint64 * 4), ("trace_unique_entries", ctypes.c_uint64),
+                ("trace_unique_vertices", ctypes.c_uint64), ("trace_unique_voxels", ctypes.c_uint64)]
 
 
 def load():
@@ -256,7 +259,11 @@ def sync(g):
 def get_stats(g) -> dict:
     s = StatsC()
     _check(load().vrt_get_stats(g, ctypes.byref(s)), g)
-    return {k: int(getattr(s, k)) for k, _ in StatsC._fields_}
+    out = {}
+    for k, _ in StatsC._fields_:
+        v = getattr(s, k)
+        out[k] = [int(x) for x in v] if k == "trace_cycles" else int(v)
+    return out
 
 
 def read_grid(g, n):

@@ -55,6 +55,10 @@ struct vrt_grid_s {
   uint32_t* order = nullptr;      // [V] pass-1 processing order of the vertices' segments
   float* shade = nullptr;         // [n^3] voxel-space shading field (brick order)
   uint32_t* shade_mask = nullptr; // [n^3 / 32] voxels the last shaded trace computed
+  // instrumented trace (VRT_OPT_TRACE_COUNTERS): bitmaps of the list entries,
+  // vertices and voxels the rays read, sized at first use
+  uint32_t *touch_list = nullptr, *touch_vert = nullptr, *touch_vox = nullptr;
+  size_t touch_list_words = 0, touch_vert_words = 0;
   bool shade_valid = false;
   // what the field was computed from: list build, pyramid build, AO, light;
   // a trace with the same inputs (a static scene) reuses it
@@ -384,6 +388,27 @@ vrt_status size_exact_queue(vrt_grid g) {
   return VRT_OK;
 }
 
+// Instrumented trace: the touch bitmaps, (re)sized for the current list
+// capacity and vertex count.
+vrt_status size_touch_bitmaps(vrt_grid g) {
+  const size_t lw = (size_t)(g->list_cap / 32 + 1), vw = (size_t)(g->V / 32 + 1);
+  const size_t nv = (size_t)g->n * g->n * g->n;
+  if (g->touch_list_words < lw) {
+    dfree(g, g->touch_list);
+    g->touch_list_words = 0;
+    VRT_CUDA(g, dalloc(g, &g->touch_list, lw));
+    g->touch_list_words = lw;
+  }
+  if (g->touch_vert_words < vw) {
+    dfree(g, g->touch_vert);
+    g->touch_vert_words = 0;
+    VRT_CUDA(g, dalloc(g, &g->touch_vert, vw));
+    g->touch_vert_words = vw;
+  }
+  if (!g->touch_vox) VRT_CUDA(g, dalloc(g, &g->touch_vox, nv / 32));
+  return VRT_OK;
+}
+
 void free_all(vrt_grid g) {
   if (g->graph_exec) {
     cudaGraphExecDestroy(g->graph_exec);
@@ -403,6 +428,8 @@ void free_all(vrt_grid g) {
   dfree(g, g->mips); dfree(g, g->vq[0]); dfree(g, g->vq[1]); dfree(g, g->pq[0]); dfree(g, g->pq[1]);
   dfree(g, g->resume);
   dfree(g, g->shade); dfree(g, g->shade_mask);
+  dfree(g, g->touch_list); dfree(g, g->touch_vert); dfree(g, g->touch_vox);
+  g->touch_list_words = g->touch_vert_words = 0;
   dfree(g, g->st);
 }
 
@@ -766,6 +793,15 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.work_next = &g->st->tr_next[0];
   a.short_list = g->short_list;
   a.ray_keys = g->ray_keys;
+  if (g->trace_counters) {  // touch bitmaps, cleared for this trace
+    if (const vrt_status ts = size_touch_bitmaps(g)) return ts;
+    VRT_CUDA(g, cudaMemsetAsync(g->touch_list, 0, g->touch_list_words * 4, g->stream));
+    VRT_CUDA(g, cudaMemsetAsync(g->touch_vert, 0, g->touch_vert_words * 4, g->stream));
+    VRT_CUDA(g, cudaMemsetAsync(g->touch_vox, 0, nv / 8, g->stream));
+    a.touch_list = g->touch_list;
+    a.touch_vert = g->touch_vert;
+    a.touch_vox = g->touch_vox;
+  }
   stage_mark(g, ST_TRACE, 0);
   g->launches += launch_trace(a, K, g->stream);
   stage_mark(g, ST_TRACE, 1);
@@ -795,6 +831,12 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
       g->launches += launch_trace(b, K, g->stream);
     }
     stage_mark(g, ST_REPAIR, 1);
+  }
+  if (g->trace_counters) {
+    VRT_CUDA(g, cudaMemsetAsync((char*)g->st + offsetof(DevStatus, tr_u_entries), 0,
+                                3 * sizeof(unsigned long long), g->stream));
+    g->launches += launch_touch_count(g->touch_list, g->touch_list_words, g->touch_vert,
+                                      g->touch_vert_words, g->touch_vox, nv / 32, g->st, g->stream);
   }
   VRT_CUDA(g, cudaGetLastError());
   return VRT_OK;
@@ -844,6 +886,13 @@ vrt_status vrt_get_stats(vrt_grid g, vrt_stats* out) {
   out->trace_capsule_tests = hs.tr_capsule;
   out->trace_voxels = hs.tr_voxels;
   out->trace_steps = hs.tr_steps;
+  out->trace_wholewarp_voxels = hs.tr_ww_voxels;
+  out->trace_wholewarp_entries = hs.tr_ww_entries;
+  out->trace_hits = hs.tr_hits;
+  for (int k = 0; k < 4; ++k) out->trace_cycles[k] = hs.tr_cycles[k];
+  out->trace_unique_entries = hs.tr_u_entries;
+  out->trace_unique_vertices = hs.tr_u_vertices;
+  out->trace_unique_voxels = hs.tr_u_voxels;
   return VRT_OK;
 }
 
@@ -971,6 +1020,9 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
       VRT_CUDA(g, dalloc(g, &g->resume, 2 * (size_t)npx));
       g->pq_cap = npx;
     }
+  }
+  if (g->trace_counters) {
+    if (const vrt_status ts = size_touch_bitmaps(g)) return ts;
   }
   if (!g->cap_stream) VRT_CUDA(g, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
   cudaStream_t user = g->stream;

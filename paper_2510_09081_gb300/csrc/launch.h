@@ -52,6 +52,9 @@ struct TraceArgs {
   uint32_t short_list;       // lists up to this length share the warp entry by entry
   uint32_t ray_keys;         // hit slots per transparent ray on that path (<= kRayKeys)
   int count;                 // accumulate trace work counters
+  uint32_t* touch_list;      // instrumented trace: bit per list entry read
+  uint32_t* touch_vert;      //   bit per vertex read (segment end points)
+  uint32_t* touch_vox;       //   bit per voxel whose words the DDA read
   const float* shade;        // voxel-space shading field [n^3] (brick order), or null
 };
 
@@ -112,6 +115,11 @@ int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off,
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
                 uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, cudaStream_t s);
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
+// Instrumented trace: the set bits of the three touch bitmaps into
+// st->tr_u_entries, tr_u_vertices, tr_u_voxels (which the caller cleared).
+int launch_touch_count(const uint32_t* list_bits, size_t list_words, const uint32_t* vert_bits,
+                       size_t vert_words, const uint32_t* vox_bits, size_t vox_words,
+                       DevStatus* st, cudaStream_t s);
 // Repair round: list the voxels of vq (count *vq_cnt), pass 2 restricted to
 // them, then clear their `need` bits and the next round's queue counters.
 int launch_repair_alloc(const GridDev& g, const uint32_t* vq, const uint32_t* vq_cnt,

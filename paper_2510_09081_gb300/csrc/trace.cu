@@ -60,6 +60,11 @@ __device__ __forceinline__ bool bit_at(const uint32_t* bits, uint32_t i) {
   return (bits[i >> 5] >> (i & 31)) & 1u;
 }
 
+// Instrumented trace: mark element i of a touch bitmap.
+__device__ __forceinline__ void touch(uint32_t* bits, uint32_t i) {
+  if (bits) atomicOr(&bits[i >> 5], 1u << (i & 31));
+}
+
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -135,6 +140,11 @@ __device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint
     set_err(A.g.st, kErrBounds);
     return ~0ull;
   }
+  if (COUNT) {
+    touch(A.touch_list, s);
+    touch(A.touch_vert, id);
+    touch(A.touch_vert, id + 1);
+  }
   const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
   if (!lines_may_meet(o, d, f3(p0), f3(p1), rrm)) return ~0ull;
   if (COUNT) ++n_cap;
@@ -159,6 +169,8 @@ struct Ray {
   uint32_t beg, end;   // pending voxel's list
   float vt0, vt1;      // pending voxel's ray interval
   unsigned n_steps, n_entries, n_cap, n_vox;  // work counters
+  unsigned n_hits, n_ww_vox, n_ww_ent;
+  unsigned long long cyc[4];  // warp cycles: DDA, shared-entry path, whole-warp path, capsule stage
 };
 
 // Parameter where the ray leaves coordinate range [lo, hi] along an axis
@@ -211,6 +223,7 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
     const float texit = fminf(tx, fminf(ty, tz));
     const uint32_t idx = brick_index(R.vx, R.vy, R.vz, A.g.log2nb);
     const uint32_t cnt = __ldg(&A.g.word[idx]) & 0xffffu;
+    if (COUNT) touch(A.touch_vox, idx);
     const float tin = R.tcur;
     // step past this voxel before returning, so the next call resumes after it
     R.tcur = texit;
@@ -281,6 +294,7 @@ __device__ void init_ray(const TraceArgs& A, Ray& R, int px, int py, bool valid)
   R.first_t = __int_as_float(0x7f800000);
   R.n_queued = 0;
   R.n_steps = R.n_entries = R.n_cap = R.n_vox = 0;
+  R.n_hits = R.n_ww_vox = R.n_ww_ent = 0;
   R.missed = false;
   R.pending = false;
   const float N = (float)A.g.n;
@@ -338,16 +352,22 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   const float t0 = __shfl_sync(FULL, R.vt0, L), t1 = __shfl_sync(FULL, R.vt1, L);
   const float r2 = A.g.r * A.g.r;
   const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
-  unsigned n_cap = 0;
+  unsigned n_cap = 0, n_hit = 0;
   if (COUNT && lane == L) {
     ++R.n_vox;
     R.n_entries += end - beg;
+    ++R.n_ww_vox;
   }
   if (OPAQUE) {
     unsigned long long best = ~0ull;
     for (uint32_t s = beg + lane; s < end; s += 32) {
       const unsigned long long k = entry_key<COUNT>(A, s, o, d, t0, t1, r2, rrm, n_cap);
+      if (COUNT && k != ~0ull) ++n_hit;
       best = k < best ? k : best;
+    }
+    if (COUNT) {
+      R.n_hits += n_hit;
+      if (lane == L) R.n_ww_ent += end - beg;
     }
     if (COUNT) R.n_cap += n_cap;
     best = warp_min_u64(best);
@@ -380,8 +400,10 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
 #pragma unroll
     for (int q = 0; q < kLaneKeys; ++q) buf[q] = ~0ull;
     bool dropped = false;
+    if (COUNT && lane == L) R.n_ww_ent += end - beg;
     for (uint32_t s = beg + lane; s < end; s += 32) {
       const unsigned long long k = entry_key<COUNT>(A, s, o, d, t0, t1, r2, rrm, n_cap);
+      if (COUNT && k != ~0ull) ++n_hit;
       if (k == ~0ull || k <= last) continue;
       if (k < buf[kLaneKeys - 1]) {
         if (buf[kLaneKeys - 1] != ~0ull) dropped = true;
@@ -446,7 +468,10 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
     // a rescan is needed only when the extraction stopped at the drop limit
     rescan = rescan && T >= kTStop && last == lim;
   }
-  if (COUNT) R.n_cap += n_cap;
+  if (COUNT) {
+    R.n_cap += n_cap;
+    R.n_hits += n_hit;
+  }
   if (lane == L) {
     R.T = T;
     R.C[0] = C0; R.C[1] = C1; R.C[2] = C2;
@@ -508,11 +533,12 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
   const uint32_t first = R.beg - (incl - glen);  // entry g of a group's list is lists[first + g]
   const float r2 = A.g.r * A.g.r;
   const float rrm = (A.g.r + 1e-3f) * (A.g.r + 1e-3f);
-  unsigned n_cap = 0;
+  unsigned n_cap = 0, n_hit = 0;
   uint2* q = s_q[tid >> 5];
   uint32_t qn = 0;  // queued pairs (warp-uniform)
   // capsule test of queued pair `lane` for lanes below cnt
   auto capsule_stage = [&](uint32_t cnt) {
+    const long long c0 = COUNT ? clock64() : 0;
     if ((uint32_t)lane < cnt) {
       const uint2 it = q[lane];
       const uint32_t id = it.x;
@@ -523,6 +549,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       const float t = capsule_entry(f3(ro), f3(rd), f3(p0), f3(p1), r2);
       if (t >= ro.w && t < rd.w && clip_keeps(A, f3(ro) + t * f3(rd), p0, p1, id)) {
         const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | id;
+        if (COUNT) ++n_hit;
         if (OPAQUE) {
           atomicMin(&s_best[wb + j], k);
         } else {
@@ -531,6 +558,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
         }
       }
     }
+    if (COUNT) R.cyc[3] += (unsigned long long)(clock64() - c0);
   };
   auto owner = [&](uint32_t gq) {
     int j = 0;
@@ -582,6 +610,10 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
       if (oka) { a0 = __ldg(&A.pos[ida]); a1 = __ldg(&A.pos[ida + 1]); }
       if (okb) { b0 = __ldg(&A.pos[idb]); b1 = __ldg(&A.pos[idb + 1]); }
+      if (COUNT) {
+        if (oka) { touch(A.touch_list, fa + ga); touch(A.touch_vert, ida); touch(A.touch_vert, ida + 1); }
+        if (okb) { touch(A.touch_list, fb + gb); touch(A.touch_vert, idb); touch(A.touch_vert, idb + 1); }
+      }
       bool pa = false, pb = false;
       if (oka) {
         const float4 ro = s_ray[0][wb + ja], rd = s_ray[1][wb + ja];
@@ -608,13 +640,20 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
     if (oka) { a0 = __ldg(&A.pos[ida]); a1 = __ldg(&A.pos[ida + 1]); }
     if (okb) { b0 = __ldg(&A.pos[idb]); b1 = __ldg(&A.pos[idb + 1]); }
+    if (COUNT) {
+      if (oka) { touch(A.touch_list, fa + ga); touch(A.touch_vert, ida); touch(A.touch_vert, ida + 1); }
+      if (okb) { touch(A.touch_list, fb + gb); touch(A.touch_vert, idb); touch(A.touch_vert, idb + 1); }
+    }
     test_group(oka ? ma : 0u, ida, a0, a1);
     test_group(okb ? mb : 0u, idb, b0, b1);
   }
   __syncwarp();
   capsule_stage(qn);
   __syncwarp();
-  if (COUNT) R.n_cap += n_cap;
+  if (COUNT) {
+    R.n_cap += n_cap;
+    R.n_hits += n_hit;
+  }
   if (!take) return;
   if (OPAQUE) {
     if (COUNT) {
@@ -674,16 +713,29 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
   if (R.T < kTStop || R.t1 < 0.0f) R.active = false;
 }
 
+// Warp cycles since `t` into the counter `c` (instrumented trace only).
+template <bool COUNT>
+__device__ __forceinline__ void lap(unsigned long long& c, long long& t) {
+  if (COUNT) {
+    const long long now = clock64();
+    c += (unsigned long long)(now - t);
+    t = now;
+  }
+}
+
 template <bool OPAQUE, bool COUNT>
 __device__ void trace_warp(const TraceArgs& A, Ray& R) {
   const int lane = threadIdx.x & 31;
+  long long t = COUNT ? clock64() : 0;
   for (;;) {
     if (R.active && !R.pending) {
       R.pending = advance<COUNT>(A, R);
       if (!R.pending) R.active = false;
     }
     if (!__any_sync(FULL, R.pending)) break;
+    lap<COUNT>(R.cyc[0], t);
     process_flat<OPAQUE, COUNT>(A, R);
+    lap<COUNT>(R.cyc[1], t);
     // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
     while (pm) {
@@ -695,7 +747,9 @@ __device__ void trace_warp(const TraceArgs& A, Ray& R) {
         if (R.t1 < 0.0f) R.active = false;
       }
     }
+    lap<COUNT>(R.cyc[2], t);
   }
+  lap<COUNT>(R.cyc[0], t);
 }
 
 template <bool COUNT>
@@ -709,11 +763,22 @@ __device__ __forceinline__ void finish(const TraceArgs& A, const Ray& R, bool va
       v += __shfl_xor_sync(FULL, v, o);
       st += __shfl_xor_sync(FULL, st, o);
     }
+    unsigned long long h = R.n_hits, wv = R.n_ww_vox, we = R.n_ww_ent;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      h += __shfl_xor_sync(FULL, h, o);
+      wv += __shfl_xor_sync(FULL, wv, o);
+      we += __shfl_xor_sync(FULL, we, o);
+    }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&A.g.st->tr_entries, e);
       atomicAdd(&A.g.st->tr_capsule, c);
       atomicAdd(&A.g.st->tr_voxels, v);
       atomicAdd(&A.g.st->tr_steps, st);
+      atomicAdd(&A.g.st->tr_hits, h);
+      atomicAdd(&A.g.st->tr_ww_voxels, wv);
+      atomicAdd(&A.g.st->tr_ww_entries, we);
+      for (int k = 0; k < 4; ++k) atomicAdd(&A.g.st->tr_cycles[k], R.cyc[k]);
     }
   }
   if (!valid) return;
@@ -740,6 +805,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_tile(TraceArgs A) {
   const int py = blockIdx.y * 16 + (warp >> 1) * 8 + (lane >> 2);
   const bool valid = px < A.cam.width && py < A.cam.height;
   Ray R;
+  R.cyc[0] = R.cyc[1] = R.cyc[2] = R.cyc[3] = 0;
   R.pix = valid ? (uint32_t)(py * A.cam.width + px) : 0u;
   init_ray(A, R, px, py, valid);
   trace_warp<OPAQUE, COUNT>(A, R);
@@ -773,7 +839,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
   Ray R;
   R.active = R.pending = false;
   R.n_steps = R.n_entries = R.n_cap = R.n_vox = 0;
-  unsigned c_steps = 0, c_entries = 0, c_cap = 0, c_vox = 0;
+  R.n_hits = R.n_ww_vox = R.n_ww_ent = 0;
+  R.cyc[0] = R.cyc[1] = R.cyc[2] = R.cyc[3] = 0;
+  unsigned c_steps = 0, c_entries = 0, c_cap = 0, c_vox = 0, c_hits = 0, c_wwv = 0, c_wwe = 0;
+  long long tclk = COUNT ? clock64() : 0;
   bool has = false;
   // Opaque main trace: refill once half the warp is idle. Queued repair
   // pixels are scattered: a warp takes at most its share of the queue, one
@@ -807,6 +876,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
           if (px < W && py < H) {
             if (COUNT) {
               c_steps += R.n_steps; c_entries += R.n_entries; c_cap += R.n_cap; c_vox += R.n_vox;
+              c_hits += R.n_hits; c_wwv += R.n_ww_vox; c_wwe += R.n_ww_ent;
             }
             R.pix = py * W + px;
             init_ray(A, R, (int)px, (int)py, true);
@@ -824,7 +894,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
       R.pending = advance<COUNT>(A, R);
       if (!R.pending) R.active = false;
     }
+    lap<COUNT>(R.cyc[0], tclk);
     process_flat<OPAQUE, COUNT>(A, R);
+    lap<COUNT>(R.cyc[1], tclk);
     // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
     while (pm) {
@@ -836,26 +908,36 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
         if (R.t1 < 0.0f) R.active = false;
       }
     }
+    lap<COUNT>(R.cyc[2], tclk);
     if (has && !R.active && !R.pending) {
       write_pixel(A, R);
       has = false;
     }
   }
   if (COUNT) {
+    lap<COUNT>(R.cyc[0], tclk);
     unsigned long long e = c_entries + R.n_entries, c = c_cap + R.n_cap, v = c_vox + R.n_vox,
-                       st = c_steps + R.n_steps;
+                       st = c_steps + R.n_steps, h = c_hits + R.n_hits, wv = c_wwv + R.n_ww_vox,
+                       we = c_wwe + R.n_ww_ent;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       e += __shfl_xor_sync(FULL, e, o);
       c += __shfl_xor_sync(FULL, c, o);
       v += __shfl_xor_sync(FULL, v, o);
       st += __shfl_xor_sync(FULL, st, o);
+      h += __shfl_xor_sync(FULL, h, o);
+      wv += __shfl_xor_sync(FULL, wv, o);
+      we += __shfl_xor_sync(FULL, we, o);
     }
     if (lane == 0) {
       atomicAdd(&A.g.st->tr_entries, e);
       atomicAdd(&A.g.st->tr_capsule, c);
       atomicAdd(&A.g.st->tr_voxels, v);
       atomicAdd(&A.g.st->tr_steps, st);
+      atomicAdd(&A.g.st->tr_hits, h);
+      atomicAdd(&A.g.st->tr_ww_voxels, wv);
+      atomicAdd(&A.g.st->tr_ww_entries, we);
+      for (int k = 0; k < 4; ++k) atomicAdd(&A.g.st->tr_cycles[k], R.cyc[k]);
     }
   }
 }
@@ -894,6 +976,26 @@ int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
     else launch_one<false, false>(a, smem, s);
   }
   return 1;
+}
+
+// --------------------------------------------------- instrumented trace
+__global__ void k_touch_count(const uint32_t* bits, size_t words, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words;
+       i += (size_t)gridDim.x * blockDim.x)
+    c += __popc(bits[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int launch_touch_count(const uint32_t* list_bits, size_t list_words, const uint32_t* vert_bits,
+                       size_t vert_words, const uint32_t* vox_bits, size_t vox_words,
+                       DevStatus* st, cudaStream_t s) {
+  k_touch_count<<<152 * 4, 256, 0, s>>>(list_bits, list_words, &st->tr_u_entries);
+  k_touch_count<<<152 * 4, 256, 0, s>>>(vert_bits, vert_words, &st->tr_u_vertices);
+  k_touch_count<<<152 * 4, 256, 0, s>>>(vox_bits, vox_words, &st->tr_u_voxels);
+  return 3;
 }
 
 // ----------------------------------------------------------------- repair

@@ -19,9 +19,11 @@
 // cannot decide go to a queue that a separate kernel decides exactly (keeping
 // the 128-bit integer path out of the hot kernels' registers).
 //
-// Pass 1 adds (occupancy code << 16) | 1 to the voxel's packed word with one
-// 32-bit atomic (Sec. 3.1) and appends the fragment as an 8-byte record
-// (voxel << 32 | segment), warp-aggregated. The paper re-voxelizes in its
+// Pass 1 adds (occupancy code << 16) | 1 to the voxel's packed word with a
+// 32-bit atomic (Sec. 3.1) -- on grids of side 512 and more one per distinct
+// voxel of a warp step, the increments of lanes that share the voxel summed
+// first -- and appends the fragment as an 8-byte record (voxel << 32 |
+// segment), warp-aggregated. The paper re-voxelizes in its
 // second pass to save memory; with the records in HBM the second pass is a
 // streaming scatter instead: for every record whose voxel received a list,
 // bump the voxel's cursor and write the segment id (Sec. 3.3).
@@ -200,16 +202,26 @@ __device__ __forceinline__ void flush_counters(DevStatus* st, unsigned long long
   }
 }
 
-__device__ __forceinline__ void add_fragment(const GridDev& g, float3 a, float3 b, float3 n0,
-                                             float3 n1, bool en0, bool en1, int x, int y, int z,
-                                             unsigned long long& F, unsigned long long& sq) {
+// The packed-word increment (occupancy code << 16) | 1 of one fragment (Alg. 3
+// at the voxel centre, quantized); counts it in F and sq.
+__device__ __forceinline__ uint32_t fragment_word(const GridDev& g, float3 a, float3 b, float3 n0,
+                                                  float3 n1, bool en0, bool en1, int x, int y,
+                                                  int z, unsigned long long& F,
+                                                  unsigned long long& sq) {
   const float3 o = make_float3((float)x, (float)y, (float)z);
   const float occ = capsule_occupancy(make_float3(0.5f, 0.5f, 0.5f), a - o, b - o, n0, n1, en0,
                                       en1, g.r_clamp, g.corr);
   const uint32_t q = (uint32_t)floorf(fmaf(g.occ_scale, occ, 0.5f));
-  atomicAdd(&g.word[brick_index(x, y, z, g.log2nb)], (q << 16) | 1u);
   F += 1;
   sq += q;
+  return (q << 16) | 1u;
+}
+
+__device__ __forceinline__ void add_fragment(const GridDev& g, float3 a, float3 b, float3 n0,
+                                             float3 n1, bool en0, bool en1, int x, int y, int z,
+                                             unsigned long long& F, unsigned long long& sq) {
+  atomicAdd(&g.word[brick_index(x, y, z, g.log2nb)],
+            fragment_word(g, a, b, n0, n1, en0, en1, x, y, z, F, sq));
 }
 
 __device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, uint32_t seg) {
@@ -251,6 +263,7 @@ __device__ __forceinline__ void flush_culled(const GridDev& g, unsigned long lon
   __syncwarp();
 }
 
+template <bool AGG>
 __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
                                                const float4* __restrict__ nrm,
                                                const uint32_t* __restrict__ order, long long V,
@@ -314,13 +327,22 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   // a kept fragment: occupancy into the packed word, record staged (all lanes call)
   auto emit = [&](bool keep, int j, const PackedWalk& p, int x, int y, int z) {
     uint32_t idx = 0;
+    const unsigned am = __ballot_sync(FULLW, keep);
     if (keep) {
       idx = brick_index(x, y, z, g.log2nb);
       const uint32_t clip = __float_as_uint(p.w3.z) >> 27;
-      add_fragment(g, f3(p.w0), f3(p.w1), f3(s_n[0][wb + j]), f3(s_n[1][wb + j]), clip & 1u,
-                   clip & 2u, x, y, z, F, sq);
+      const uint32_t inc = fragment_word(g, f3(p.w0), f3(p.w1), f3(s_n[0][wb + j]),
+                                         f3(s_n[1][wb + j]), clip & 1u, clip & 2u, x, y, z, F, sq);
+      if (AGG) {
+        // lanes adding to the same voxel (neighbouring segments of the warp
+        // share voxels) sum their increments: one atomic per voxel and step
+        const unsigned peers = __match_any_sync(am, idx);
+        const uint32_t sum = __reduce_add_sync(peers, inc);
+        if (lane == __ffs(peers) - 1) atomicAdd(&g.word[idx], sum);
+      } else {
+        atomicAdd(&g.word[idx], inc);
+      }
     }
-    const unsigned am = __ballot_sync(FULLW, keep);
     if (keep) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg_of(j);
     wcount += __popc(am);
     if (wcount > kWarpRecords - 32) {
@@ -412,7 +434,10 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t i) {
 
 // Pass 2: stream the fragment records; mode 0 lists every fragment, mode 1
 // those whose voxel the cull marked, mode 2 (repair) those whose voxel's
-// `need` bit is set. Mode 1 also copies the records of unmarked voxels to the
+// `need` bit is set. (One returning cursor atomic per listed record: merging
+// the lanes of a warp that list into the same voxel first, by a match on the
+// voxel index, measured slower -- the match costs more than the atomics it
+// saves.) Mode 1 also copies the records of unmarked voxels to the
 // (by then unused) exact-path queue, warp-staged, so that the repair rounds
 // stream only those; when they do not all fit, the repair streams every record.
 __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint32_t* __restrict__ need,
@@ -474,7 +499,12 @@ int launch_pass1(const float4* pos, const float4* nrm, const uint32_t* order, lo
                  const GridDev& g, cudaStream_t s) {
   if (V < 2) return 0;
   const int T = 256;
-  k_pass1<<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
+  // Grids of side 512 and more keep their packed words (512 MB) in DRAM, where
+  // merging the increments of lanes that share a voxel pays (ABC pathlines,
+  // 512^3: pass 1 7.8 -> 7.4 ms); at 256^3 the words stay in L2 and the match
+  // costs more than the atomics it saves (bundles: 2.3 -> 3.5 ms).
+  if (g.n >= 512) k_pass1<true><<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
+  else k_pass1<false><<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
   k_exact1<<<152 * 4, T, 0, s>>>(pos, nrm, g);
   return 2;
 }

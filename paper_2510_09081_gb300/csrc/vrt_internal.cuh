@@ -66,6 +66,14 @@ struct DevStatus {
   unsigned long long tr_steps;       // DDA steps (voxels and empty bricks)
   unsigned int tr_next[kMaxRepairRounds + 1];  // work items handed out per trace launch
   unsigned int tr_pad;
+  unsigned long long tr_ww_voxels;   // voxel lists taken by the whole-warp path
+  unsigned long long tr_ww_entries;  // entries it examined (rescans included)
+  unsigned long long tr_hits;        // accepted hits (keys a ray received)
+  unsigned long long tr_cycles[4];   // warp cycles: DDA, shared-entry path, whole-warp path,
+                                     // and the capsule tests within the shared-entry path
+  // distinct list entries, vertices and voxel words the rays of the last
+  // instrumented trace read (its repair rounds included)
+  unsigned long long tr_u_entries, tr_u_vertices, tr_u_voxels;
 };
 
 // -------------------------------------------------------------- grid layout
@@ -362,7 +370,7 @@ __device__ __forceinline__ float ball_entry(float3 oc, float3 d, float r2) {
   const float bq = dot3(oc, d);
   const float3 w = oc - bq * d;
   const float disc = r2 - dot3(w, w);
-  return disc >= 0.0f ? -bq - sqrtf(disc) : __int_as_float(0x7f800000);
+  return disc >= 0.0f ? -bq - (disc > 0.0f ? disc * rsqrtf(disc) : 0.0f) : __int_as_float(0x7f800000);
 }
 
 // First entry of the line o + t d (|d| = 1) into the capsule (a, b, r); +inf
@@ -378,17 +386,18 @@ __device__ __forceinline__ float capsule_entry(float3 o, float3 d, float3 a, flo
   const float3 ba = b - a;
   const float L2 = dot3(ba, ba);
   if (!(L2 > 0.0f)) return ball_entry(oa, d, r2);
-  const float inv = 1.0f / L2;
+  const float inv = __fdividef(1.0f, L2);
   const float3 dp = d - (dot3(d, ba) * inv) * ba;
   const float3 op = oa - (dot3(oa, ba) * inv) * ba;
   const float A = dot3(dp, dp);
-  if (!(A > 0.0f))  // along the axis: the nearer ball
+  if (!(A > 1e-30f))  // along the axis: the nearer ball
     return fminf(ball_entry(oa, d, r2), ball_entry(o - b, d, r2));
-  const float ts = -dot3(op, dp) / A;
+  const float ts = __fdividef(-dot3(op, dp), A);
   const float3 w = op + ts * dp;
   const float disc = r2 - dot3(w, w);
   if (disc < 0.0f) return __int_as_float(0x7f800000);
-  const float t = ts - sqrtf(disc / A);
+  const float q = __fdividef(disc, A);
+  const float t = ts - (q > 0.0f ? q * rsqrtf(q) : 0.0f);
   const float y = dot3(oa + t * d, ba);
   if (y < 0.0f) return ball_entry(oa, d, r2);
   if (y > L2) return ball_entry(o - b, d, r2);
