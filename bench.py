@@ -319,6 +319,8 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     vrt.set_option(r.h, vrt.OPT_GRAPH, 0 if args.no_graph else 1)
+    hit_key = vrt.HIT_KEY_16_16 if args.hit_key == "16+16" else vrt.HIT_KEY_DEPTH_ID
+    vrt.set_option(r.h, vrt.OPT_HIT_KEY, hit_key)
     static_cams = None
     if args.static:
         # lists (and the pyramid) built once, for every occupied voxel; each
@@ -400,6 +402,7 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(s2):
             r2.upload(xyz_dev, ls.offsets)
         vrt.set_option(r2.h, vrt.OPT_GRAPH, 0 if args.no_graph else 1)
+        vrt.set_option(r2.h, vrt.OPT_HIT_KEY, hit_key)
         vrt.set_option(r2.h, vrt.OPT_MIPS_FORMAT, {"fp32": vrt.MIPS_F32, "fp16": vrt.MIPS_F16,
                                                    "bf16": vrt.MIPS_BF16}[args.mips])
         outs2 = (torch.empty_like(rgba), torch.empty_like(fid), torch.empty_like(ft))
@@ -482,6 +485,7 @@ def run_ours(args, rank, world, local_rank):
         "impl": "ours",
         "config": {"workload": wl["desc"] + (f" [scaled to {args.scale} of the lines]" if args.scale != 1.0 else "")
                    + (f" [occupancy pyramid in {args.mips}]" if args.mips != "fp32" else "")
+                   + (" [hits ordered by the 16+16-bit per-voxel key]" if args.hit_key == "16+16" else "")
                    + (f" [voxel-space shading: AO x shadow toward {SHADING_LIGHT}]"
                       if args.shading == "voxel" else "")
                    + (" [static scene: lists built once for every occupied voxel; each frame "
@@ -697,6 +701,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hit-key", choices=("depth-id", "16+16"), default="depth-id",
+                    help="order of a ray's hits within a voxel (16+16: the paper's 32-bit key)")
     ap.add_argument("--no-serving", action="store_true",
                     help="leave the serving leg out of the bundles line")
     ap.add_argument("--no-graph", action="store_true",

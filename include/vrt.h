@@ -277,7 +277,15 @@ vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host)
  * VRT_OPT_TRACE_RAY_KEYS (9): value in [1, 40] (default 40): hit slots per
  * transparent ray and voxel on the shared-entry path; a ray with more hits in
  * one voxel takes the whole-warp path for it. The image does not depend on
- * it; for testing. */
+ * it; for testing.
+ * VRT_OPT_HIT_KEY (10): the order of the hits a ray composites within one
+ * voxel (Sec. 3.5). VRT_HIT_KEY_DEPTH_ID (default): by depth in fp32, equal
+ * depths by segment id -- the ground-truth order, independent of how the list
+ * build ordered each list. VRT_HIT_KEY_16_16: the paper's 32-bit key, the
+ * hit's depth within the voxel's ray interval quantized to 16 bits above its
+ * 16-bit index in the voxel's list, so hits whose depths fall in the same
+ * 1/65536 of the interval follow the list's order (which the list build's
+ * atomics leave arbitrary); depths and shading still use the exact hit. */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
 #define VRT_OPT_TRACE_COUNTERS 3
@@ -287,6 +295,9 @@ vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host)
 #define VRT_OPT_TEST_SCAN_STALL 7
 #define VRT_OPT_TRACE_SHORT_LIST 8
 #define VRT_OPT_TRACE_RAY_KEYS 9
+#define VRT_OPT_HIT_KEY 10
+#define VRT_HIT_KEY_DEPTH_ID 0
+#define VRT_HIT_KEY_16_16 1
 #define VRT_MIPS_F32 0
 #define VRT_MIPS_F16 1
 #define VRT_MIPS_BF16 2

@@ -30,6 +30,8 @@ OPT_CULL_DEPTH = 6
 OPT_TEST_SCAN_STALL = 7
 OPT_TRACE_SHORT_LIST = 8
 OPT_TRACE_RAY_KEYS = 9
+OPT_HIT_KEY = 10
+HIT_KEY_DEPTH_ID, HIT_KEY_16_16 = 0, 1
 NOALLOC_GAVE_UP, NOALLOC_WRAPPED = 1, 2   # status bits of scan_counts_noalloc
 MIPS_F32, MIPS_F16, MIPS_BF16 = 0, 1, 2
 STAGES = ["ingest", "pass1", "mips", "cull", "scan", "pass2", "trace", "repair", "shade"]

@@ -87,6 +87,7 @@ struct vrt_grid_s {
   int scan_stall = -1;      // VRT_OPT_TEST_SCAN_STALL (-1: off)
   uint32_t short_list = kShortList;  // VRT_OPT_TRACE_SHORT_LIST
   uint32_t ray_keys = kRayKeys;      // VRT_OPT_TRACE_RAY_KEYS
+  int key16 = 0;                     // VRT_OPT_HIT_KEY
   bool use_graph = false;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -793,6 +794,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.work_next = &g->st->tr_next[0];
   a.short_list = g->short_list;
   a.ray_keys = g->ray_keys;
+  a.key16 = g->key16;
   if (g->trace_counters) {  // touch bitmaps, cleared for this trace
     if (const vrt_status ts = size_touch_bitmaps(g)) return ts;
     VRT_CUDA(g, cudaMemsetAsync(g->touch_list, 0, g->touch_list_words * 4, g->stream));
@@ -1159,6 +1161,12 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
     if (value < 0 || value > (int64_t)kShortList)
       return fail(g, VRT_ERR_INVALID_ARG, "short-list limit must be in [0, 1024]");
     g->short_list = (uint32_t)value;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_HIT_KEY) {
+    if (value != VRT_HIT_KEY_DEPTH_ID && value != VRT_HIT_KEY_16_16)
+      return fail(g, VRT_ERR_INVALID_ARG, "hit key must be VRT_HIT_KEY_DEPTH_ID or VRT_HIT_KEY_16_16");
+    g->key16 = value == VRT_HIT_KEY_16_16;
     return VRT_OK;
   }
   if (option == VRT_OPT_TRACE_RAY_KEYS) {

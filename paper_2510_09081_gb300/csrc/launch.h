@@ -51,6 +51,7 @@ struct TraceArgs {
                              // (C, T), (first id bits, first t, voxel index bits, entry t)
   uint32_t short_list;       // lists up to this length share the warp entry by entry
   uint32_t ray_keys;         // hit slots per transparent ray on that path (<= kRayKeys)
+  int key16;                 // order hits by the paper's 16+16-bit per-voxel key
   int count;                 // accumulate trace work counters
   uint32_t* touch_list;      // instrumented trace: bit per list entry read
   uint32_t* touch_vert;      //   bit per vertex read (segment end points)

@@ -116,6 +116,32 @@ __device__ __forceinline__ float3 tangent_colour(const TraceArgs& A, uint32_t id
   return make_float3(fabsf(dv.x) * il, fabsf(dv.y) * il, fabsf(dv.z) * il);
 }
 
+// Sort key of an accepted hit at depth t of segment id, entry li of the voxel's
+// list, the voxel's ray interval being [t0, t1). Default: the depth's fp32 bits
+// above the id (depth order, ties by id). With A.key16 the paper's per-voxel
+// key (Sec. 3.5): the depth within the voxel quantized to 16 bits above the
+// 16-bit list index -- hits of equal quantized depth then follow the list's
+// order -- with the id below it, for shading.
+template <bool KEY16>
+__device__ __forceinline__ unsigned long long hit_key(float t, uint32_t id, uint32_t li, float t0,
+                                                      float t1) {
+  if (!KEY16) return ((unsigned long long)__float_as_uint(t) << 32) | id;
+  const float u = __fdividef(t - t0, t1 - t0);
+  const uint32_t q = min(65535u, (uint32_t)fmaxf(0.0f, u * 65536.0f));
+  return ((unsigned long long)((q << 16) | (li & 0xffffu)) << 32) | id;
+}
+
+// Depth of the hit a key names: stored in the default key; recomputed from the
+// segment with the 16+16 key, which keeps only its quantized position.
+template <bool KEY16>
+__device__ __forceinline__ float hit_depth(const TraceArgs& A, unsigned long long k, float3 o,
+                                           float3 d) {
+  if (!KEY16) return __uint_as_float((uint32_t)(k >> 32));
+  const uint32_t id = (uint32_t)(k & 0xffffffffu);
+  const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
+  return capsule_entry(o, d, f3(p0), f3(p1), A.g.r * A.g.r);
+}
+
 __device__ __forceinline__ bool clip_keeps(const TraceArgs& A, float3 P, float4 p0, float4 p1,
                                            uint32_t id) {
   if (__float_as_uint(p0.w) & kClipOn) {
@@ -131,10 +157,10 @@ __device__ __forceinline__ bool clip_keeps(const TraceArgs& A, float3 P, float4 
 
 // Key of list entry s for ray (o, d) over [t0, t1): depth bits << 32 | id, or
 // ~0 when the segment gives no accepted hit there.
-template <bool COUNT>
-__device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint32_t s, float3 o,
-                                                        float3 d, float t0, float t1, float r2,
-                                                        float rrm, unsigned& n_cap) {
+template <bool COUNT, bool KEY16>
+__device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint32_t s, uint32_t beg,
+                                                        float3 o, float3 d, float t0, float t1,
+                                                        float r2, float rrm, unsigned& n_cap) {
   const uint32_t id = __ldg(&A.g.lists[s]);
   if (id + 1 >= A.n_vert) {
     set_err(A.g.st, kErrBounds);
@@ -151,7 +177,7 @@ __device__ __forceinline__ unsigned long long entry_key(const TraceArgs& A, uint
   const float t = capsule_entry(o, d, f3(p0), f3(p1), r2);
   if (!(t >= t0 && t < t1)) return ~0ull;
   if (!clip_keeps(A, o + t * d, p0, p1, id)) return ~0ull;
-  return ((unsigned long long)__float_as_uint(t) << 32) | id;
+  return hit_key<KEY16>(t, id, s - beg, t0, t1);
 }
 
 // Per-lane ray state. Components are kept as scalars (no runtime-indexed
@@ -344,7 +370,7 @@ __device__ void resume_ray(const TraceArgs& A, Ray& R) {
 }
 
 // The warp processes the pending voxel of lane `L`.
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   const int lane = threadIdx.x & 31;
   const float3 o = shfl3(R.o, L), d = shfl3(R.d, L);
@@ -361,7 +387,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
   if (OPAQUE) {
     unsigned long long best = ~0ull;
     for (uint32_t s = beg + lane; s < end; s += 32) {
-      const unsigned long long k = entry_key<COUNT>(A, s, o, d, t0, t1, r2, rrm, n_cap);
+      const unsigned long long k = entry_key<COUNT, KEY16>(A, s, beg, o, d, t0, t1, r2, rrm, n_cap);
       if (COUNT && k != ~0ull) ++n_hit;
       best = k < best ? k : best;
     }
@@ -373,7 +399,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
     best = warp_min_u64(best);
     if (best != ~0ull) {
       const uint32_t id = (uint32_t)(best & 0xffffffffu);
-      const float t = __uint_as_float((uint32_t)(best >> 32));
+      const float t = hit_depth<KEY16>(A, best, o, d);
       float3 c = tangent_colour(A, id);
       if (A.ao) c = (A.ao == 2 ? shade_at(A, o + t * d) : ao_warp(A, o + t * d)) * c;
       if (lane == L) {
@@ -402,7 +428,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
     bool dropped = false;
     if (COUNT && lane == L) R.n_ww_ent += end - beg;
     for (uint32_t s = beg + lane; s < end; s += 32) {
-      const unsigned long long k = entry_key<COUNT>(A, s, o, d, t0, t1, r2, rrm, n_cap);
+      const unsigned long long k = entry_key<COUNT, KEY16>(A, s, beg, o, d, t0, t1, r2, rrm, n_cap);
       if (COUNT && k != ~0ull) ++n_hit;
       if (k == ~0ull || k <= last) continue;
       if (k < buf[kLaneKeys - 1]) {
@@ -444,7 +470,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
       float tq = 0.0f;
       if (lane < n_out) {
         const uint32_t id = (uint32_t)(mine & 0xffffffffu);
-        tq = __uint_as_float((uint32_t)(mine >> 32));
+        tq = hit_depth<KEY16>(A, mine, o, d);
         c = tangent_colour(A, id);
         if (A.ao) c = hit_shade(A, o + tq * d) * c;
       }
@@ -452,6 +478,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
       for (int q = 0; q < n_out; ++q) {
         const float3 cq = shfl3(c, q);
         const unsigned long long kq = __shfl_sync(FULL, mine, q);
+        const float tqq = KEY16 ? __shfl_sync(FULL, tq, q) : 0.0f;
         if (T < kTStop) break;
         const float w = T * A.alpha;
         C0 = fmaf(w, cq.x, C0);
@@ -460,7 +487,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
         T *= om;
         if (fid < 0) {
           fid = (int)(kq & 0xffffffffu);
-          ft = __uint_as_float((uint32_t)(kq >> 32));
+          ft = KEY16 ? tqq : __uint_as_float((uint32_t)(kq >> 32));
         }
         last = kq;
       }
@@ -494,7 +521,7 @@ __device__ void process_voxel(const TraceArgs& A, Ray& R, int L) {
 // ray, sorted and composited by the ray's own lane afterwards). A transparent
 // ray with more hits in the voxel keeps its voxel pending for the whole-warp
 // path, which starts it again from scratch.
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 __device__ void process_flat(const TraceArgs& A, Ray& R) {
   extern __shared__ unsigned long long s_key[];  // [kRayKeys][kTraceThreads]
   __shared__ float4 s_ray[2][kTraceThreads];      // (o, t_enter), (d, t_exit)
@@ -542,13 +569,13 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     if ((uint32_t)lane < cnt) {
       const uint2 it = q[lane];
       const uint32_t id = it.x;
-      const int j = (int)it.y;
+      const int j = (int)(it.y & 255u);
       const float4 p0 = __ldg(&A.pos[id]), p1 = __ldg(&A.pos[id + 1]);
       const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
       if (COUNT) ++n_cap;
       const float t = capsule_entry(f3(ro), f3(rd), f3(p0), f3(p1), r2);
       if (t >= ro.w && t < rd.w && clip_keeps(A, f3(ro) + t * f3(rd), p0, p1, id)) {
-        const unsigned long long k = ((unsigned long long)__float_as_uint(t) << 32) | id;
+        const unsigned long long k = hit_key<KEY16>(t, id, it.y >> 8, ro.w, rd.w);
         if (COUNT) ++n_hit;
         if (OPAQUE) {
           atomicMin(&s_best[wb + j], k);
@@ -567,9 +594,10 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       if (__shfl_sync(FULL, incl, j + st - 1) <= gq) j += st;
     return min(j, 31);
   };
-  auto append = [&](bool pass, uint32_t id, int j) {
+  // queue entry: segment id, owner lane j | list index li << 8 (16+16 keys)
+  auto append = [&](bool pass, uint32_t id, int j, uint32_t li) {
     const unsigned m = __ballot_sync(FULL, pass);
-    if (pass) q[qn + __popc(m & lt)] = make_uint2(id, (uint32_t)j);
+    if (pass) q[qn + __popc(m & lt)] = make_uint2(id, (uint32_t)j | (li << 8));
     qn += __popc(m);
     if (qn >= 32) {
       __syncwarp();
@@ -581,7 +609,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     }
   };
   // line tests of a loaded entry against the rays in mask m, one per round
-  auto test_group = [&](unsigned m, uint32_t id, float4 p0, float4 p1) {
+  auto test_group = [&](unsigned m, uint32_t id, float4 p0, float4 p1, uint32_t li) {
     while (__any_sync(FULL, m)) {
       bool pass = false;
       int j = 0;
@@ -591,7 +619,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
         const float4 ro = s_ray[0][wb + j], rd = s_ray[1][wb + j];
         pass = lines_may_meet(f3(ro), f3(rd), f3(p0), f3(p1), rrm);
       }
-      append(pass, id, j);
+      append(pass, id, j, li);
     }
   };
   // two independent (owner search, list load, vertex loads) chains per step:
@@ -623,8 +651,13 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
         const float4 ro = s_ray[0][wb + jb], rd = s_ray[1][wb + jb];
         pb = lines_may_meet(f3(ro), f3(rd), f3(b0), f3(b1), rrm);
       }
-      append(pa, ida, ja);
-      append(pb, idb, jb);
+      uint32_t la = 0, lb = 0;  // list indices (16+16 keys)
+      if (KEY16) {
+        la = fa + ga - __shfl_sync(FULL, R.beg, ja);
+        lb = fb + gb - __shfl_sync(FULL, R.beg, jb);
+      }
+      append(pa, ida, ja, la);
+      append(pb, idb, jb, lb);
     }
   } else for (uint32_t t0 = 0; t0 < total; t0 += 64) {
     const uint32_t ga = t0 + lane, gb = ga + 32;
@@ -644,8 +677,13 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
       if (oka) { touch(A.touch_list, fa + ga); touch(A.touch_vert, ida); touch(A.touch_vert, ida + 1); }
       if (okb) { touch(A.touch_list, fb + gb); touch(A.touch_vert, idb); touch(A.touch_vert, idb + 1); }
     }
-    test_group(oka ? ma : 0u, ida, a0, a1);
-    test_group(okb ? mb : 0u, idb, b0, b1);
+    uint32_t la = 0, lb = 0;  // list indices (16+16 keys)
+    if (KEY16) {
+      la = fa + ga - __shfl_sync(FULL, R.beg, ja);
+      lb = fb + gb - __shfl_sync(FULL, R.beg, jb);
+    }
+    test_group(oka ? ma : 0u, ida, a0, a1, la);
+    test_group(okb ? mb : 0u, idb, b0, b1, lb);
   }
   __syncwarp();
   capsule_stage(qn);
@@ -663,7 +701,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
     const unsigned long long best = s_best[tid];
     if (best != ~0ull) {
       const uint32_t id = (uint32_t)(best & 0xffffffffu);
-      const float t = __uint_as_float((uint32_t)(best >> 32));
+      const float t = hit_depth<KEY16>(A, best, R.o, R.d);
       float3 c = tangent_colour(A, id);
       if (A.ao) c = hit_shade(A, R.o + t * R.d) * c;
       R.C[0] = A.alpha * c.x; R.C[1] = A.alpha * c.y; R.C[2] = A.alpha * c.z;
@@ -696,7 +734,7 @@ __device__ void process_flat(const TraceArgs& A, Ray& R) {
   for (uint32_t q = 0; q < nk && R.T >= kTStop; ++q) {
     const unsigned long long kq = kb[q * kTraceThreads];
     const uint32_t id = (uint32_t)(kq & 0xffffffffu);
-    const float t = __uint_as_float((uint32_t)(kq >> 32));
+    const float t = hit_depth<KEY16>(A, kq, R.o, R.d);
     float3 c = tangent_colour(A, id);
     if (A.ao) c = hit_shade(A, R.o + t * R.d) * c;
     const float w = R.T * A.alpha;
@@ -723,7 +761,7 @@ __device__ __forceinline__ void lap(unsigned long long& c, long long& t) {
   }
 }
 
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 __device__ void trace_warp(const TraceArgs& A, Ray& R) {
   const int lane = threadIdx.x & 31;
   long long t = COUNT ? clock64() : 0;
@@ -734,14 +772,14 @@ __device__ void trace_warp(const TraceArgs& A, Ray& R) {
     }
     if (!__any_sync(FULL, R.pending)) break;
     lap<COUNT>(R.cyc[0], t);
-    process_flat<OPAQUE, COUNT>(A, R);
+    process_flat<OPAQUE, COUNT, KEY16>(A, R);
     lap<COUNT>(R.cyc[1], t);
     // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
     while (pm) {
       const int L = __ffs(pm) - 1;
       pm &= pm - 1;
-      process_voxel<OPAQUE, COUNT>(A, R, L);
+      process_voxel<OPAQUE, COUNT, KEY16>(A, R, L);
       if (lane == L) {
         R.pending = false;
         if (R.t1 < 0.0f) R.active = false;
@@ -797,7 +835,7 @@ __device__ __forceinline__ void finish(const TraceArgs& A, const Ray& R, bool va
 // tall (a block 2x2 tiles), and its lanes write their pixels together at the
 // end. Measured faster than persistent refilling here, since the tile's rays
 // share lists (and slightly faster than 8x4 or 16x2 tiles).
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 __global__ void __launch_bounds__(kTraceThreads) k_trace_tile(TraceArgs A) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -808,7 +846,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_tile(TraceArgs A) {
   R.cyc[0] = R.cyc[1] = R.cyc[2] = R.cyc[3] = 0;
   R.pix = valid ? (uint32_t)(py * A.cam.width + px) : 0u;
   init_ray(A, R, px, py, valid);
-  trace_warp<OPAQUE, COUNT>(A, R);
+  trace_warp<OPAQUE, COUNT, KEY16>(A, R);
   finish<COUNT>(A, R, valid);
 }
 
@@ -830,7 +868,7 @@ __device__ __forceinline__ void write_pixel(const TraceArgs& A, const Ray& R) {
 // atomic per refill). Work item w of the image is pixel (w mod 32) of the
 // (w / 32)-th 8x4 tile, so a full refill is a coherent tile; in the repair
 // re-trace, item w is the w-th queued pixel.
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
   const int lane = threadIdx.x & 31;
   const uint32_t W = (uint32_t)A.cam.width, H = (uint32_t)A.cam.height;
@@ -895,14 +933,14 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
       if (!R.pending) R.active = false;
     }
     lap<COUNT>(R.cyc[0], tclk);
-    process_flat<OPAQUE, COUNT>(A, R);
+    process_flat<OPAQUE, COUNT, KEY16>(A, R);
     lap<COUNT>(R.cyc[1], tclk);
     // long lists: the whole warp on one list at a time
     unsigned pm = __ballot_sync(FULL, R.pending);
     while (pm) {
       const int L = __ffs(pm) - 1;
       pm &= pm - 1;
-      process_voxel<OPAQUE, COUNT>(A, R, L);
+      process_voxel<OPAQUE, COUNT, KEY16>(A, R, L);
       if (lane == L) {
         R.pending = false;
         if (R.t1 < 0.0f) R.active = false;
@@ -943,37 +981,43 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
 }
 
 // Persistent grid: as many blocks as can be resident at once.
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 int persistent_blocks(size_t smem) {
   static int blocks = 0;  // per instantiation; the device does not change under a grid
   if (!blocks) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<OPAQUE, COUNT>, kTraceThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<OPAQUE, COUNT, KEY16>, kTraceThreads, smem);
     blocks = max(1, sms) * max(1, per_sm);
   }
   return blocks;
 }
 
-template <bool OPAQUE, bool COUNT>
+template <bool OPAQUE, bool COUNT, bool KEY16>
 void launch_one(const TraceArgs& a, size_t smem, cudaStream_t s) {
   if (!OPAQUE && !a.pix_list) {
     const dim3 grid((a.cam.width + 7) / 8, (a.cam.height + 15) / 16);
-    k_trace_tile<OPAQUE, COUNT><<<grid, kTraceThreads, smem, s>>>(a);
+    k_trace_tile<OPAQUE, COUNT, KEY16><<<grid, kTraceThreads, smem, s>>>(a);
   } else {
-    k_trace<OPAQUE, COUNT><<<persistent_blocks<OPAQUE, COUNT>(smem), kTraceThreads, smem, s>>>(a);
+    k_trace<OPAQUE, COUNT, KEY16><<<persistent_blocks<OPAQUE, COUNT, KEY16>(smem), kTraceThreads, smem, s>>>(a);
   }
+}
+
+template <bool COUNT, bool KEY16>
+void launch_mode(const TraceArgs& a, int K, size_t smem, cudaStream_t s) {
+  if (K == 1) launch_one<true, COUNT, KEY16>(a, smem, s);
+  else launch_one<false, COUNT, KEY16>(a, smem, s);
 }
 
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s) {
   const size_t smem = K == 1 ? 0 : sizeof(unsigned long long) * kRayKeys * kTraceThreads;
   if (a.count) {
-    if (K == 1) launch_one<true, true>(a, smem, s);
-    else launch_one<false, true>(a, smem, s);
+    if (a.key16) launch_mode<true, true>(a, K, smem, s);
+    else launch_mode<true, false>(a, K, smem, s);
   } else {
-    if (K == 1) launch_one<true, false>(a, smem, s);
-    else launch_one<false, false>(a, smem, s);
+    if (a.key16) launch_mode<false, true>(a, K, smem, s);
+    else launch_mode<false, false>(a, K, smem, s);
   }
   return 1;
 }

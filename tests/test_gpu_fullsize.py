@@ -94,6 +94,37 @@ def test_fullsize_sampled_pixels(frame):
     assert res["hits"] >= 100, res
 
 
+def test_fullsize_paper_hit_key(frame):
+    """The paper's 16+16-bit per-voxel hit key on the full frame: hits whose
+    depths fall into the same 1/65536 of a voxel's ray interval follow the
+    list's (arbitrary) order instead of their exact depths. Counted against the
+    default (depth, id) key over the whole image, and checked against the
+    oracle's ground truth on the sampled pixels."""
+    cam, r, o = frame["cam"], frame["r"], frame["oracle"]
+    vrt.set_option(r.h, vrt.OPT_HIT_KEY, vrt.HIT_KEY_16_16)
+    try:
+        rgba, fid, ft = r.frame(cam, alpha=0.3, cull_on=1, voxelize_first=False)
+        vrt.sync(r.h)
+    finally:
+        vrt.set_option(r.h, vrt.OPT_HIT_KEY, vrt.HIT_KEY_DEPTH_ID)
+    rgba = rgba.cpu().numpy().reshape(-1, 4)
+    fid = fid.cpu().numpy().reshape(-1)
+    ft = ft.cpu().numpy().reshape(-1)
+    npx = cam.width * cam.height
+    d = np.abs(rgba - frame["rgba"]).max(1)
+    changed = int((d > 0).sum())
+    print(f"16+16 key: {changed} of {npx} pixels differ from the (depth, id) key, max "
+          f"|dRGBA| {d.max():.2e}; first ids differ at {int((fid != frame['fid']).sum())}")
+    assert changed <= 1e-3 * npx
+    cy, cx = cam.height // 2, cam.width // 2
+    block = ((cy - 4 + np.arange(8))[:, None] * cam.width + (cx - 8 + np.arange(16))[None, :]).ravel()
+    pix = np.unique(np.concatenate([np.random.default_rng(7).choice(npx, 320, replace=False), block]))
+    ref = o.render_pixels(cam, pix, alpha=0.3, brute=True)
+    res = compare_image(rgba[pix], fid[pix], ft[pix], ref)
+    assert res["col_bad"] == 0 and res["id_bad"] == 0, res
+    assert res["max_t_rel"] < 2e-4, res
+
+
 def test_fullsize_culling_never_changes_the_image(frame):
     cam, r = frame["cam"], frame["r"]
     rgba, fid, ft = r.frame(cam, alpha=0.3, cull_on=0, voxelize_first=False)

@@ -142,3 +142,35 @@ def test_scan_wait_gives_up_and_the_grid_recovers():
     r.close()
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.3, 0.1])
+def test_paper_hit_key_matches_oracle(alpha):
+    """The paper's 32-bit hit key (VRT_OPT_HIT_KEY = 16+16: the depth within the
+    voxel quantized to 16 bits above the fragment's list index) against the
+    oracle's ground-truth order, within the parity tolerances; the pixels where
+    its order differs from the default (depth, id) key are few."""
+    ls = tiny_walks(n_lines=600, n_verts=40, seed=123)
+    cam = _persp_cam()
+    ref = oracle.Oracle.from_lineset(ls).render(cam, alpha=alpha)
+    r = vrt.Renderer(ls.n, ls.radius)
+    r.upload(ls.xyz, ls.offsets)
+    default = _image(r, cam, alpha)
+    vrt.set_option(r.h, vrt.OPT_HIT_KEY, vrt.HIT_KEY_16_16)
+    k16 = _image(r, cam, alpha)
+    with pytest.raises(vrt.VrtError):
+        vrt.set_option(r.h, vrt.OPT_HIT_KEY, 2)
+    vrt.set_option(r.h, vrt.OPT_HIT_KEY, vrt.HIT_KEY_DEPTH_ID)
+    again = _image(r, cam, alpha)
+    r.close()
+    res = compare_image(*k16, ref)
+    assert res["hits"] > 2000
+    _assert_parity(res)
+    changed = int(np.any(default[0] != k16[0], axis=-1).sum())
+    assert changed <= 0.001 * res["n"], changed
+    # ids and depths of the first hits: the same hits, exact depths
+    same_first = default[1] == k16[1]
+    assert same_first.mean() > 0.999
+    assert np.array_equal(default[2][same_first], k16[2][same_first])
+    for a, b in zip(default, again):
+        assert np.array_equal(a, b)
