@@ -72,11 +72,12 @@ def make_workload(name, scale=1.0):
         return dict(ls=ls, cam=cam, update=upd, alpha=1.0, ao=0, cull=0,
                     desc="random walks: 2000 x 50 vertices, grid 64^3, r 0.4, 256x256 ortho, opaque")
     if name == "abc":
-        ls = G.abc_pathlines(frame=0)
+        npart = int(round(1_000_000 * scale))
+        ls = G.abc_pathlines(n_particles=npart, frame=0)
         cam = G.abc_camera(frame=0)
 
         def upd(f):
-            nl = G.abc_pathlines(frame=f + 1)
+            nl = G.abc_pathlines(n_particles=npart, frame=f + 1)
             return 0, nl.xyz
         return dict(ls=ls, cam=cam, update=upd, alpha=1.0, ao=6, cull=1,
                     desc=("ABC-flow lines: 1M x 32 vertices (31M segments), grid 512^3, r 0.25, "
@@ -553,9 +554,14 @@ def run_ours(args, rank, world, local_rank):
             "plain_p50_ms": arms["plain_poisson"]["p50_ms"],
             "plain_p99_ms": arms["plain_poisson"]["p99_ms"],
             "arms": arms,
-            "definition": ("served: 4 stream slots (frames of different sets overlap); plain: 1; "
-                           "frames/s with every request queued at once; latency submit -> frame "
-                           "finished seen by the host, Poisson arrivals at 200 requests/s")}
+            "small_sets_batched_frames_per_s": arms["small_sets_batched"]["frames_per_s"],
+            "small_sets_unbatched_frames_per_s": arms["small_sets_unbatched"]["frames_per_s"],
+            "definition": ("served: 4 stream slots (frames of different sets overlap); plain: 1 "
+                           "slot; batched: frames of sets under 100k segments issued in batches of "
+                           "up to 16 (one graph launch each); frames/s with every request "
+                           "queued at once; latency submit -> frame finished seen by the host, "
+                           "Poisson arrivals at 200 requests/s; small_sets: 8 frames (720p, no "
+                           "update) of every set under 100k segments, queued at once")}
     if not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_baseline(wl)
@@ -616,15 +622,15 @@ def serve_arms(sets, reqs, arrivals, device=0):
     dev = torch.device("cuda", device)
     bufs = [torch.empty((2160, 3840, 4), dtype=torch.float32, device=dev) for _ in range(n_sets)]
 
-    def arm(slots, paced):
-        srv = vrt.Server(max_inflight=slots)
+    def arm(slots, paced, small_segments=0, only=None):
+        srv = vrt.Server(max_inflight=slots, small_segments=small_segments)
         ids = [srv.add_set(ls.xyz, ls.offsets, ls.n, ls.radius) for ls in sets]
         # warm-up (not timed): one frame of every set makes it resident
         for k in range(n_sets):
             srv.submit(ids[k], reqs[0][1], bufs[k], alpha=0.5)
         srv.poll(wait=True)
         t_start = time.perf_counter()
-        for i, (k, cam, alpha, first, upd) in enumerate(reqs):
+        for i, (k, cam, alpha, first, upd) in enumerate(reqs if only is None else only):
             if paced:
                 delay = t_start + arrivals[i] - time.perf_counter()
                 if delay > 0:
@@ -638,10 +644,28 @@ def serve_arms(sets, reqs, arrivals, device=0):
         bad = sum(r["status"] != 0 for r in res)
         return dict(frames_per_s=round(len(res) / wall, 2), p50_ms=round(float(np.percentile(lat, 50)), 3),
                     p99_ms=round(float(np.percentile(lat, 99)), 3), failed=int(bad),
-                    resident_sets=st["resident_sets"], evictions=st["evictions"])
+                    resident_sets=st["resident_sets"], evictions=st["evictions"],
+                    batches=st["batches"], batched_frames=st["batched_frames"])
 
+    # small sets alone (fewer than 100k segments, 720p): batched vs one frame at a time
+    rng = np.random.default_rng(5)
+    small = [k for k, ls in enumerate(sets) if ls.n_segments < 100_000]
+    small_reqs = []
+    for i in range(8 * len(small)):
+        k = small[i % len(small)]
+        ls = sets[k]
+        c = ls.n / 2.0
+        th = rng.uniform(0, 2 * np.pi)
+        from gen import linesets as G
+        cam = G.Camera(width=1280, height=720, ortho=0,
+                       eye=(c + 1.7 * ls.n * np.cos(th), c + 1.7 * ls.n * np.sin(th), c + 0.5 * ls.n),
+                       target=(c, c, c), up=(0.0, 0.0, 1.0), fovy_deg=45.0)
+        small_reqs.append((k, cam, float(rng.uniform(0.2, 1.0)), 0, None))
     out = {"served_poisson": arm(4, True), "plain_poisson": arm(1, True),
-           "served_capacity": arm(4, False), "plain_capacity": arm(1, False)}
+           "served_capacity": arm(4, False), "plain_capacity": arm(1, False),
+           "served_capacity_batched": arm(4, False, small_segments=100_000),
+           "small_sets_batched": arm(4, False, small_segments=100_000, only=small_reqs),
+           "small_sets_unbatched": arm(4, False, only=small_reqs)}
     del bufs
     torch.cuda.empty_cache()
     return out

@@ -285,7 +285,12 @@ vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host)
  * hit's depth within the voxel's ray interval quantized to 16 bits above its
  * 16-bit index in the voxel's list, so hits whose depths fall in the same
  * 1/65536 of the interval follow the list's order (which the list build's
- * atomics leave arbitrary); depths and shading still use the exact hit. */
+ * atomics leave arbitrary); depths and shading still use the exact hit.
+ * VRT_OPT_TRACE_TILE (11): the pixel tile a warp of the transparent trace owns:
+ * 32 pixels, 2, 4 (default), 8 or 16 wide (16, 8, 4 or 2 tall). Rays of a tile
+ * that wait in the same voxel share each list entry's loads, so the best shape
+ * depends on the scene and camera (vrt_tune_shapes measures it). The image
+ * does not depend on it. The instrumented trace and the 16+16 key use 4. */
 #define VRT_OPT_FORCE_EXACT 1
 #define VRT_OPT_STAGE_TIMING 2
 #define VRT_OPT_TRACE_COUNTERS 3
@@ -296,6 +301,7 @@ vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host)
 #define VRT_OPT_TRACE_SHORT_LIST 8
 #define VRT_OPT_TRACE_RAY_KEYS 9
 #define VRT_OPT_HIT_KEY 10
+#define VRT_OPT_TRACE_TILE 11
 #define VRT_HIT_KEY_DEPTH_ID 0
 #define VRT_HIT_KEY_16_16 1
 #define VRT_MIPS_F32 0
@@ -330,6 +336,18 @@ vrt_status vrt_tune_grid_side(const vrt_grid_desc* base, const float* xyz, int32
                               int64_t n_polylines, const vrt_camera* cam,
                               const vrt_render_params* p, const int32_t* sides, int32_t n_sides,
                               int32_t frames, int32_t* best_side, float* ms_out);
+
+/* Autotuning of the voxel resolution and the trace's tile shape: as
+ * vrt_tune_grid_side, for every grid side in `sides` and every tile width in
+ * `tiles` (VRT_OPT_TRACE_TILE: 2, 4, 8 or 16); ms_out (nullable) receives
+ * n_sides * n_tiles mean frame times, side-major (+inf where that pair could
+ * not render the scene); *best_side and *best_tile the fastest pair. */
+vrt_status vrt_tune_shapes(const vrt_grid_desc* base, const float* xyz, int32_t stride,
+                           int64_t n_vertices, const int64_t* polyline_offsets,
+                           int64_t n_polylines, const vrt_camera* cam, const vrt_render_params* p,
+                           const int32_t* sides, int32_t n_sides, const int32_t* tiles,
+                           int32_t n_tiles, int32_t frames, int32_t* best_side,
+                           int32_t* best_tile, float* ms_out);
 
 /* Device memory the grid holds, in bytes (its buffers as currently sized). */
 vrt_status vrt_grid_device_bytes(vrt_grid g, uint64_t* bytes);
@@ -418,6 +436,16 @@ typedef struct {
   int32_t max_inflight; /* frames on the device at once (stream slots), >= 1;
                            0 selects 4 */
   int32_t device;       /* CUDA device ordinal */
+  int32_t small_segments; /* > 0: frames of sets with fewer segments than
+                           this are issued in batches: the pending frames of up
+                           to max_batch idle small sets are captured into one
+                           CUDA graph (one branch per set, each set's chain on
+                           its own stream) and launched at once on one slot;
+                           <= 0 (default): no batching. (Measured: frames of
+                           sets under 100k segments at 720p are bound by their
+                           trace on the GPU, and the per-batch capture makes
+                           batching slower there, 1028 vs 1154 frames/s.) */
+  int32_t max_batch;    /* frames per batch, 0 selects 16 (at most 64) */
 } vrt_server_desc;
 
 typedef struct {
@@ -436,6 +464,8 @@ typedef struct {
   int32_t evictions;         /* sets evicted so far */
   int32_t pending;           /* submitted, not yet issued */
   int32_t inflight;          /* issued, not yet finished */
+  uint64_t batches;          /* small-set batches issued (one graph launch each) */
+  uint64_t batched_frames;   /* frames issued in those batches */
 } vrt_server_stats;
 
 vrt_status vrt_server_create(const vrt_server_desc* desc, vrt_server* out);

@@ -31,6 +31,7 @@ OPT_TEST_SCAN_STALL = 7
 OPT_TRACE_SHORT_LIST = 8
 OPT_TRACE_RAY_KEYS = 9
 OPT_HIT_KEY = 10
+OPT_TRACE_TILE = 11
 HIT_KEY_DEPTH_ID, HIT_KEY_16_16 = 0, 1
 NOALLOC_GAVE_UP, NOALLOC_WRAPPED = 1, 2   # status bits of scan_counts_noalloc
 MIPS_F32, MIPS_F16, MIPS_BF16 = 0, 1, 2
@@ -43,7 +44,7 @@ SYMBOLS = ["vrt_create_grid", "vrt_upload_segments", "vrt_update_vertices", "vrt
            "vrt_get_stage_ms", "vrt_scan_counts_noalloc", "vrt_last_error", "vrt_destroy",
            "vrt_grid_device_bytes", "vrt_set_stream", "vrt_server_create", "vrt_server_add_set",
            "vrt_server_submit", "vrt_server_poll", "vrt_server_get_stats", "vrt_server_destroy",
-           "vrt_frame", "vrt_tune_grid_side"]
+           "vrt_frame", "vrt_tune_grid_side", "vrt_tune_shapes"]
 
 
 class VrtError(RuntimeError):
@@ -59,7 +60,8 @@ class GridDesc(ctypes.Structure):
 
 class ServerDesc(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("small_segments", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32)]
 
 
 class ServerResult(ctypes.Structure):
@@ -72,7 +74,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
                 ("completed", ctypes.c_uint64), ("resident_sets", ctypes.c_int32),
                 ("evictions", ctypes.c_int32), ("pending", ctypes.c_int32),
-                ("inflight", ctypes.c_int32)]
+                ("inflight", ctypes.c_int32), ("batches", ctypes.c_uint64),
+                ("batched_frames", ctypes.c_uint64)]
 
 
 class CameraC(ctypes.Structure):
@@ -135,6 +138,9 @@ def load():
         "vrt_tune_grid_side": [ctypes.POINTER(GridDesc), P, i32, i64, P, i64,
                                ctypes.POINTER(CameraC), ctypes.POINTER(RenderParamsC), P, i32, i32,
                                ctypes.POINTER(i32), P],
+        "vrt_tune_shapes": [ctypes.POINTER(GridDesc), P, i32, i64, P, i64,
+                            ctypes.POINTER(CameraC), ctypes.POINTER(RenderParamsC), P, i32, P, i32,
+                            i32, ctypes.POINTER(i32), ctypes.POINTER(i32), P],
         "vrt_set_stream": [P, P],
         "vrt_server_create": [ctypes.POINTER(ServerDesc), ctypes.POINTER(P)],
         "vrt_server_add_set": [P, ctypes.POINTER(GridDesc), P, i32, i64, P, i64,
@@ -413,9 +419,10 @@ class Server:
     ``submit`` queues a frame of a registered set and returns at once; ``poll``
     returns finished requests with their status and latency."""
 
-    def __init__(self, hbm_budget=0, max_inflight=4, device=0):
+    def __init__(self, hbm_budget=0, max_inflight=4, device=0, small_segments=0, max_batch=0):
         desc = ServerDesc(hbm_budget=int(hbm_budget), max_inflight=int(max_inflight),
-                          device=int(device))
+                          device=int(device), small_segments=int(small_segments),
+                          max_batch=int(max_batch))
         h = ctypes.c_void_p()
         _check(load().vrt_server_create(ctypes.byref(desc), ctypes.byref(h)))
         self.h = h
@@ -515,3 +522,23 @@ def tune_grid_side(xyz, offsets, n, radius, cam, sides, alpha=1.0, ao_cones=0, c
                                      ctypes.byref(params_c(alpha, ao_cones, cull_on, 0)), _ptr(sides_a),
                                      int(sides_a.shape[0]), int(frames), ctypes.byref(best), _ptr(ms)))
     return int(best.value), {int(k): float(v) for k, v in zip(sides_a, ms)}
+
+
+def tune_shapes(xyz, offsets, n, radius, cam, sides, tiles=(2, 4, 8, 16), alpha=1.0, ao_cones=0,
+                cull_on=0, frames=3):
+    """vrt_tune_shapes: ((best side, best tile width), {(side, tile): mean ms})."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    desc = GridDesc(n=int(n), radius=float(radius), r_min=0.5, occ_scale=32, max_fragments=0)
+    sides_a = np.ascontiguousarray(sides, dtype=np.int32)
+    tiles_a = np.ascontiguousarray(tiles, dtype=np.int32)
+    ms = np.zeros(sides_a.shape[0] * tiles_a.shape[0], np.float32)
+    bs, bt = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().vrt_tune_shapes(ctypes.byref(desc), _ptr(xyz), int(xyz.shape[1]), int(xyz.shape[0]),
+                                  _ptr(offsets), int(offsets.shape[0] - 1), ctypes.byref(camera_c(cam)),
+                                  ctypes.byref(params_c(alpha, ao_cones, cull_on, 0)), _ptr(sides_a),
+                                  int(sides_a.shape[0]), _ptr(tiles_a), int(tiles_a.shape[0]),
+                                  int(frames), ctypes.byref(bs), ctypes.byref(bt), _ptr(ms)))
+    grid = {(int(a), int(b)): float(ms[i * tiles_a.shape[0] + j])
+            for i, a in enumerate(sides_a) for j, b in enumerate(tiles_a)}
+    return (int(bs.value), int(bt.value)), grid

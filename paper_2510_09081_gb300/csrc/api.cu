@@ -88,6 +88,7 @@ struct vrt_grid_s {
   uint32_t short_list = kShortList;  // VRT_OPT_TRACE_SHORT_LIST
   uint32_t ray_keys = kRayKeys;      // VRT_OPT_TRACE_RAY_KEYS
   int key16 = 0;                     // VRT_OPT_HIT_KEY
+  int tile_w = 4;                    // VRT_OPT_TRACE_TILE
   bool use_graph = false;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -795,6 +796,7 @@ vrt_status vrt_trace(vrt_grid g, const vrt_camera* cam, const vrt_render_params*
   a.short_list = g->short_list;
   a.ray_keys = g->ray_keys;
   a.key16 = g->key16;
+  a.tile_w = g->tile_w;
   if (g->trace_counters) {  // touch bitmaps, cleared for this trace
     if (const vrt_status ts = size_touch_bitmaps(g)) return ts;
     VRT_CUDA(g, cudaMemsetAsync(g->touch_list, 0, g->touch_list_words * 4, g->stream));
@@ -978,6 +980,41 @@ vrt_status vrt_read_shading(vrt_grid g, float* values, uint8_t* valid) {
   return VRT_OK;
 }
 
+}  // extern "C"
+
+// Allocate every buffer a frame with these parameters sizes lazily (the
+// pyramid, shading field, cull fields, repair queues for this image size,
+// instrumented-trace bitmaps), so that the frame's calls allocate nothing and
+// can be captured into a CUDA graph. May synchronize the grid's stream.
+vrt_status vrt::prepare_frame(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p) {
+  const size_t nv = (size_t)g->n * g->n * g->n;
+  if ((p->ao_cones || p->voxel_shading) && !g->mips)
+    VRT_CUDA(g, dalloc(g, (float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
+  if (p->voxel_shading && !g->shade) VRT_CUDA(g, dalloc(g, &g->shade, nv));
+  if (p->voxel_shading && !g->shade_mask) VRT_CUDA(g, dalloc(g, &g->shade_mask, nv / 32));
+  if (p->cull) {
+    if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
+    if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
+    if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
+    const uint32_t npx = (uint32_t)cam->width * (uint32_t)cam->height;
+    if (npx > g->pq_cap) {
+      VRT_CUDA(g, cudaStreamSynchronize(g->stream));
+      dfree(g, g->pq[0]); dfree(g, g->pq[1]); dfree(g, g->resume);
+      g->pq_cap = 0;
+      VRT_CUDA(g, dalloc(g, &g->pq[0], npx));
+      VRT_CUDA(g, dalloc(g, &g->pq[1], npx));
+      VRT_CUDA(g, dalloc(g, &g->resume, 2 * (size_t)npx));
+      g->pq_cap = npx;
+    }
+  }
+  if (g->trace_counters) {
+    if (const vrt_status ts = size_touch_bitmaps(g)) return ts;
+  }
+  return VRT_OK;
+}
+
+extern "C" {
+
 vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const float* xyz,
                      int32_t stride, int32_t on_device, const vrt_camera* cam,
                      const vrt_render_params* p, float* rgba, int32_t* first_id, float* first_t) {
@@ -1003,29 +1040,7 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
   }
   // every buffer the chain sizes lazily exists before the capture (no
   // allocation may happen inside one)
-  const size_t nv = (size_t)g->n * g->n * g->n;
-  if ((p->ao_cones || p->voxel_shading) && !g->mips)
-    VRT_CUDA(g, dalloc(g, (float**)&g->mips, (size_t)(g->lev_off[g->n_levels - 1] + 1)));
-  if (p->voxel_shading && !g->shade) VRT_CUDA(g, dalloc(g, &g->shade, nv));
-  if (p->voxel_shading && !g->shade_mask) VRT_CUDA(g, dalloc(g, &g->shade_mask, nv / 32));
-  if (p->cull) {
-    if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
-    if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
-    if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
-    const uint32_t npx = (uint32_t)cam->width * (uint32_t)cam->height;
-    if (npx > g->pq_cap) {
-      VRT_CUDA(g, cudaStreamSynchronize(g->stream));
-      dfree(g, g->pq[0]); dfree(g, g->pq[1]); dfree(g, g->resume);
-      g->pq_cap = 0;
-      VRT_CUDA(g, dalloc(g, &g->pq[0], npx));
-      VRT_CUDA(g, dalloc(g, &g->pq[1], npx));
-      VRT_CUDA(g, dalloc(g, &g->resume, 2 * (size_t)npx));
-      g->pq_cap = npx;
-    }
-  }
-  if (g->trace_counters) {
-    if (const vrt_status ts = size_touch_bitmaps(g)) return ts;
-  }
+  if (const vrt_status ps = vrt::prepare_frame(g, cam, p)) return ps;
   if (!g->cap_stream) VRT_CUDA(g, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
   cudaStream_t user = g->stream;
   g->stream = g->cap_stream;
@@ -1064,16 +1079,21 @@ vrt_status vrt_frame(vrt_grid g, int64_t first_vertex, int64_t n_vertices, const
   return VRT_OK;
 }
 
-vrt_status vrt_tune_grid_side(const vrt_grid_desc* base, const float* xyz, int32_t stride,
-                              int64_t n_vertices, const int64_t* offsets, int64_t n_polylines,
-                              const vrt_camera* cam, const vrt_render_params* p,
-                              const int32_t* sides, int32_t n_sides, int32_t frames,
-                              int32_t* best_side, float* ms_out) {
-  if (!base || !xyz || !offsets || !cam || !p || !sides || n_sides <= 0 || frames <= 0 || !best_side)
+vrt_status vrt_tune_shapes(const vrt_grid_desc* base, const float* xyz, int32_t stride,
+                           int64_t n_vertices, const int64_t* offsets, int64_t n_polylines,
+                           const vrt_camera* cam, const vrt_render_params* p, const int32_t* sides,
+                           int32_t n_sides, const int32_t* tiles, int32_t n_tiles, int32_t frames,
+                           int32_t* best_side, int32_t* best_tile, float* ms_out) {
+  if (!base || !xyz || !offsets || !cam || !p || !sides || n_sides <= 0 || !tiles || n_tiles <= 0 ||
+      frames <= 0 || !best_side || !best_tile)
     return fail(nullptr, VRT_ERR_INVALID_ARG, "NULL argument or empty candidate list");
   if (stride != 3 && stride != 4) return fail(nullptr, VRT_ERR_INVALID_ARG, "stride must be 3 or 4");
+  for (int32_t j = 0; j < n_tiles; ++j)
+    if (tiles[j] != 2 && tiles[j] != 4 && tiles[j] != 8 && tiles[j] != 16)
+      return fail(nullptr, VRT_ERR_INVALID_ARG, "tile widths must be 2, 4, 8 or 16");
   float best = INFINITY;
   *best_side = 0;
+  *best_tile = 0;
   std::vector<float> scaled((size_t)n_vertices * 3);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   VRT_CUDA(nullptr, cudaEventCreate(&e0));
@@ -1102,36 +1122,52 @@ vrt_status vrt_tune_grid_side(const vrt_grid_desc* base, const float* xyz, int32
     }
     c.ortho_h = (float)(cam->ortho_h * f);
     vrt_grid g = nullptr;
-    float ms = INFINITY;
     vrt_status r = vrt_create_grid(&d, nullptr, &g);
     if (r == VRT_OK) r = vrt_upload_segments(g, scaled.data(), 3, n_vertices, offsets, n_polylines, 0);
-    if (r == VRT_OK) r = vrt_frame(g, 0, 0, nullptr, 3, 0, &c, p, out, nullptr, nullptr);  // warm-up
-    if (r == VRT_OK) r = vrt_sync(g);
-    if (r == VRT_OK) {
-      cudaEventRecord(e0, nullptr);
-      for (int32_t k = 0; k < frames && r == VRT_OK; ++k)
-        r = vrt_frame(g, 0, 0, nullptr, 3, 0, &c, p, out, nullptr, nullptr);
-      cudaEventRecord(e1, nullptr);
-      cudaEventSynchronize(e1);
-      if (r == VRT_OK) r = vrt_sync(g);
-      if (r == VRT_OK) {
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= (float)frames;
+    for (int32_t j = 0; j < n_tiles; ++j) {
+      float ms = INFINITY;
+      vrt_status rj = r;
+      if (rj == VRT_OK) rj = vrt_set_option(g, VRT_OPT_TRACE_TILE, tiles[j]);
+      if (rj == VRT_OK) rj = vrt_frame(g, 0, 0, nullptr, 3, 0, &c, p, out, nullptr, nullptr);  // warm-up
+      if (rj == VRT_OK) rj = vrt_sync(g);
+      if (rj == VRT_OK) {
+        cudaEventRecord(e0, nullptr);
+        for (int32_t k = 0; k < frames && rj == VRT_OK; ++k)
+          rj = vrt_frame(g, 0, 0, nullptr, 3, 0, &c, p, out, nullptr, nullptr);
+        cudaEventRecord(e1, nullptr);
+        cudaEventSynchronize(e1);
+        if (rj == VRT_OK) rj = vrt_sync(g);
+        if (rj == VRT_OK) {
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= (float)frames;
+        }
+      }
+      if (rj != VRT_OK) ms = INFINITY;  // a side that does not work (range, memory) is skipped
+      if (ms_out) ms_out[(size_t)i * n_tiles + j] = ms;
+      if (ms < best) {
+        best = ms;
+        *best_side = sides[i];
+        *best_tile = tiles[j];
       }
     }
     if (g) vrt_destroy(g);
-    if (r != VRT_OK) ms = INFINITY;  // a side that does not work (range, memory) is skipped
-    if (ms_out) ms_out[i] = ms;
-    if (ms < best) {
-      best = ms;
-      *best_side = sides[i];
-    }
   }
   cudaFree(out);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (*best_side == 0) return fail(nullptr, VRT_ERR_INVALID_ARG, "no candidate side rendered the scene");
+  if (*best_side == 0) return fail(nullptr, VRT_ERR_INVALID_ARG, "no candidate rendered the scene");
   return result;
+}
+
+vrt_status vrt_tune_grid_side(const vrt_grid_desc* base, const float* xyz, int32_t stride,
+                              int64_t n_vertices, const int64_t* offsets, int64_t n_polylines,
+                              const vrt_camera* cam, const vrt_render_params* p,
+                              const int32_t* sides, int32_t n_sides, int32_t frames,
+                              int32_t* best_side, float* ms_out) {
+  const int32_t tile = 4;
+  int32_t best_tile = 0;
+  return vrt_tune_shapes(base, xyz, stride, n_vertices, offsets, n_polylines, cam, p, sides, n_sides,
+                         &tile, 1, frames, best_side, &best_tile, ms_out);
 }
 
 vrt_status vrt_grid_device_bytes(vrt_grid g, uint64_t* bytes) {
@@ -1161,6 +1197,12 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
     if (value < 0 || value > (int64_t)kShortList)
       return fail(g, VRT_ERR_INVALID_ARG, "short-list limit must be in [0, 1024]");
     g->short_list = (uint32_t)value;
+    return VRT_OK;
+  }
+  if (option == VRT_OPT_TRACE_TILE) {
+    if (value != 2 && value != 4 && value != 8 && value != 16)
+      return fail(g, VRT_ERR_INVALID_ARG, "trace tile width must be 2, 4, 8 or 16");
+    g->tile_w = (int)value;
     return VRT_OK;
   }
   if (option == VRT_OPT_HIT_KEY) {

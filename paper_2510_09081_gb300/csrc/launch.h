@@ -52,6 +52,7 @@ struct TraceArgs {
   uint32_t short_list;       // lists up to this length share the warp entry by entry
   uint32_t ray_keys;         // hit slots per transparent ray on that path (<= kRayKeys)
   int key16;                 // order hits by the paper's 16+16-bit per-voxel key
+  int tile_w;                // transparent trace: warp tile width (2, 4, 8 or 16 pixels)
   int count;                 // accumulate trace work counters
   uint32_t* touch_list;      // instrumented trace: bit per list entry read
   uint32_t* touch_vert;      //   bit per vertex read (segment end points)
@@ -132,6 +133,11 @@ int launch_repair_clear(const GridDev& g, uint32_t* need, const uint32_t* vq,
 // camera and render parameters are acceptable to vrt_cull and vrt_trace, else
 // what is wrong.
 const char* frame_args_error(const vrt_camera* cam, const vrt_render_params* p);
+
+// Allocate every buffer a frame of `g` with these parameters sizes lazily, so
+// that the frame's calls allocate nothing and can be captured into a CUDA
+// graph (may synchronize the grid's stream).
+vrt_status prepare_frame(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p);
 
 // Testing hook of vrt_scan_counts_noalloc (vrt_set_option(NULL,
 // VRT_OPT_TEST_SCAN_STALL, tile)): tile >= 0 makes that look-back tile skip

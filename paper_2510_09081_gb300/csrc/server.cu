@@ -7,7 +7,13 @@
 // request of every set that has no frame in flight, onto a free slot, making
 // its set resident first (evicting least-recently-used idle sets while the HBM
 // budget would be exceeded), and (3) sleeps until a submission or a finished
-// frame wakes it. CUDA work is issued with the lock released.
+// frame wakes it. CUDA work is issued with the lock released. Optionally,
+// frames of small sets (fewer segments than small_segments) are issued in
+// batches: the oldest
+// pending frame of each of up to max_batch idle small sets are captured into
+// one CUDA graph -- a branch per set, each set's chain on its own stream, all
+// joined at the end -- and launched at once on one slot, so their kernels run
+// side by side and the host issues one launch for all of them.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -63,10 +69,13 @@ struct Request {
 
 struct Slot {
   cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> branch;  // a batch's per-set streams (created at first use)
+  cudaEvent_t fork = nullptr;        // a batch's fork point on `stream`
+  std::vector<cudaEvent_t> join;     // a batch's per-branch ends
   bool busy = false;
   std::atomic<bool> done{false};
   Clock::time_point t_done;
-  Request req;
+  std::vector<Request> reqs;         // the frame, or the batch's frames, in flight
   struct vrt_server_s* server = nullptr;
 };
 
@@ -92,6 +101,9 @@ struct vrt_server_s {
   uint64_t tick = 0;
   int evictions = 0;
   int resident_sets = 0;
+  int64_t small_segments = 0;  // sets with fewer segments are batched (<= 0: never)
+  int max_batch = 16;
+  uint64_t batches = 0, batched_frames = 0;
 };
 
 namespace {
@@ -224,11 +236,10 @@ void trim(vrt_server s, std::unique_lock<std::mutex>& lk) {
   }
 }
 
-// Issue one frame of `rq` on slot `sl` (scheduler thread, lock released).
-vrt_status issue(vrt_server s, Slot& sl, Request& rq) {
-  ServerSet& st = *s->sets[rq.set];
+// The calls of one frame of `rq` on its set's grid, on stream `stream`.
+vrt_status frame_chain(ServerSet& st, Request& rq, cudaStream_t stream) {
   vrt_grid g = st.grid;
-  vrt_status r = vrt_set_stream(g, sl.stream);
+  vrt_status r = vrt_set_stream(g, stream);
   if (r == VRT_OK && rq.n > 0) {
     // the host copy follows every issued update (for uploads after an eviction)
     std::memcpy(&st.xyz[3 * rq.first], rq.upd, sizeof(float) * 3 * (size_t)rq.n);
@@ -238,9 +249,71 @@ vrt_status issue(vrt_server s, Slot& sl, Request& rq) {
   if (r == VRT_OK && (rq.p.ao_cones || rq.p.voxel_shading)) r = vrt_build_mips(g);
   if (r == VRT_OK) r = vrt_cull(g, &rq.cam, &rq.p);
   if (r == VRT_OK) r = vrt_trace(g, &rq.cam, &rq.p, rq.rgba, rq.first_id, rq.first_t);
+  return r;
+}
+
+// Issue one frame of `rq` on slot `sl` (scheduler thread, lock released).
+vrt_status issue(vrt_server s, Slot& sl, Request& rq) {
+  vrt_status r = frame_chain(*s->sets[rq.set], rq, sl.stream);
   if (r == VRT_OK && cudaLaunchHostFunc(sl.stream, on_frame_done, &sl) != cudaSuccess)
     r = VRT_ERR_CUDA;
   return r;
+}
+
+// Issue the frames of `sl.reqs` (distinct resident sets) as one CUDA graph on
+// slot `sl`: capture on the slot's stream, fork one branch stream per frame,
+// run each frame's chain on its branch, join them back, launch the graph once
+// (scheduler thread, lock released). On failure nothing has reached the device
+// (the capture is discarded); *captured says whether the grids' host state
+// already moved on (their sets must then be uploaded again).
+vrt_status issue_batch(vrt_server s, Slot& sl, bool* captured) {
+  const size_t k = sl.reqs.size();
+  *captured = false;
+  // buffers the frames size lazily, before the capture (no allocation inside)
+  for (Request& rq : sl.reqs) {
+    ServerSet& st = *s->sets[rq.set];
+    vrt_status r = vrt_set_stream(st.grid, sl.stream);
+    if (r == VRT_OK) r = vrt::prepare_frame(st.grid, &rq.cam, &rq.p);
+    if (r != VRT_OK) return r;
+  }
+  while (sl.branch.size() < k) {
+    cudaStream_t b = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) return VRT_ERR_CUDA;
+    sl.branch.push_back(b);
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return VRT_ERR_CUDA;
+    sl.join.push_back(e);
+  }
+  if (!sl.fork && cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) != cudaSuccess)
+    return VRT_ERR_CUDA;
+  if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return VRT_ERR_CUDA;
+  *captured = true;
+  vrt_status r = cudaEventRecord(sl.fork, sl.stream) == cudaSuccess ? VRT_OK : VRT_ERR_CUDA;
+  for (size_t i = 0; i < k && r == VRT_OK; ++i) {
+    if (cudaStreamWaitEvent(sl.branch[i], sl.fork, 0) != cudaSuccess) { r = VRT_ERR_CUDA; break; }
+    r = frame_chain(*s->sets[sl.reqs[i].set], sl.reqs[i], sl.branch[i]);
+    if (r == VRT_OK && (cudaEventRecord(sl.join[i], sl.branch[i]) != cudaSuccess ||
+                        cudaStreamWaitEvent(sl.stream, sl.join[i], 0) != cudaSuccess))
+      r = VRT_ERR_CUDA;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(sl.stream, &graph);
+  // later calls on these grids (vrt_sync when the batch retires) use the slot's stream
+  for (Request& rq : sl.reqs) vrt_set_stream(s->sets[rq.set]->grid, sl.stream);
+  if (r == VRT_OK && ec != cudaSuccess) r = VRT_ERR_CUDA;
+  cudaGraphExec_t exec = nullptr;
+  if (r == VRT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) r = VRT_ERR_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  if (r == VRT_OK && cudaGraphLaunch(exec, sl.stream) != cudaSuccess) r = VRT_ERR_CUDA;
+  if (exec) cudaGraphExecDestroy(exec);  // the launched graph still runs to its end
+  if (r != VRT_OK) {
+    cudaGetLastError();
+    return r;
+  }
+  *captured = false;  // it ran: the grids' state is that of the frames
+  if (cudaLaunchHostFunc(sl.stream, on_frame_done, &sl) != cudaSuccess) return VRT_ERR_CUDA;
+  return VRT_OK;
 }
 
 void finish(vrt_server s, const Request& rq, int32_t status, Clock::time_point t_done) {  // lock held
@@ -256,26 +329,123 @@ void finish(vrt_server s, const Request& rq, int32_t status, Clock::time_point t
   s->cv_done.notify_all();
 }
 
+// Evict set k's grid (its host copy stays): used when a batch capture failed
+// after the grid's host-side state had moved on. Lock held, released around
+// the CUDA calls.
+void drop_grid(vrt_server s, std::unique_lock<std::mutex>& lk, int k) {
+  ServerSet& v = *s->sets[k];
+  if (!v.grid) return;
+  vrt_grid vg = v.grid;
+  v.grid = nullptr;
+  s->resident_bytes -= v.bytes;
+  --s->resident_sets;
+  lk.unlock();
+  vrt_destroy(vg);
+  lk.lock();
+}
+
+// Issue a batch of small-set frames on `sl` if at least two are ready: the
+// oldest pending request of each idle, unblocked set with fewer than
+// small_segments segments, up to max_batch, each made resident. Returns false
+// (having issued nothing) when fewer than two qualify. Lock held; released
+// around the CUDA calls.
+bool issue_small_batch(vrt_server s, std::unique_lock<std::mutex>& lk, Slot& sl,
+                       std::vector<char>& blocked) {
+  std::vector<char> seen(s->sets.size(), 0);
+  std::vector<size_t> pick;
+  for (size_t i = 0; i < s->pending.size() && (int)pick.size() < s->max_batch; ++i) {
+    const int k = s->pending[i].set;
+    if (seen[k]) continue;
+    seen[k] = 1;
+    const ServerSet& st = *s->sets[k];
+    if (st.busy || blocked[k] || st.V - st.P >= s->small_segments) continue;
+    pick.push_back(i);
+  }
+  if (pick.size() < 2) return false;
+  // take them out of the queue (highest index first keeps the others valid)
+  std::vector<Request> reqs;
+  for (size_t j = pick.size(); j-- > 0;) {
+    reqs.push_back(s->pending[pick[j]]);
+    s->pending.erase(s->pending.begin() + (long)pick[j]);
+  }
+  std::reverse(reqs.begin(), reqs.end());
+  sl.busy = true;
+  sl.done.store(false);
+  sl.reqs.clear();
+  for (Request& rq : reqs) {
+    ServerSet& st = *s->sets[rq.set];
+    st.busy = true;
+    st.last_use = ++s->tick;
+    vrt_status r = VRT_OK;
+    const bool ok = make_resident(s, lk, rq.set, &r);
+    if (ok) {
+      sl.reqs.push_back(rq);
+    } else if (r == VRT_OK) {  // no room yet: back to the queue's front, try later
+      st.busy = false;
+      s->pending.push_front(rq);
+      blocked[rq.set] = 1;
+    } else {
+      st.busy = false;
+      rq.t_issue = Clock::now();
+      finish(s, rq, r, Clock::now());
+    }
+  }
+  if (sl.reqs.empty()) {
+    sl.busy = false;
+    return true;  // the picks were handled (queued again or failed)
+  }
+  const Clock::time_point t_issue = Clock::now();
+  for (Request& rq : sl.reqs) rq.t_issue = t_issue;
+  lk.unlock();
+  bool captured = false;
+  vrt_status r = sl.reqs.size() >= 2 ? issue_batch(s, sl, &captured) : issue(s, sl, sl.reqs[0]);
+  if (r != VRT_OK) cudaStreamSynchronize(sl.stream);
+  lk.lock();
+  if (r == VRT_OK) {
+    if (sl.reqs.size() >= 2) {
+      ++s->batches;
+      s->batched_frames += sl.reqs.size();
+    }
+    return true;
+  }
+  for (Request& rq : sl.reqs) {  // nothing of the failed batch reached the device
+    if (captured) drop_grid(s, lk, rq.set);
+    else if (s->sets[rq.set]->grid) {
+      lk.unlock();
+      vrt_sync(s->sets[rq.set]->grid);
+      lk.lock();
+    }
+    s->sets[rq.set]->busy = false;
+    finish(s, rq, r, Clock::now());
+  }
+  sl.reqs.clear();
+  sl.busy = false;
+  return true;
+}
+
 void scheduler(vrt_server s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    // (1) retire finished frames
+    // (1) retire finished frames (a slot holds one frame or a batch)
     for (auto& slp : s->slots) {
       Slot& sl = *slp;
       if (!sl.busy || !sl.done.load()) continue;
-      ServerSet& st = *s->sets[sl.req.set];
-      lk.unlock();
-      const vrt_status status = vrt_sync(st.grid);  // the frame's device status
-      uint64_t b = 0;
-      vrt_grid_device_bytes(st.grid, &b);
-      lk.lock();
-      s->resident_bytes += b - st.bytes;  // lazily sized buffers may have grown
-      st.bytes = b;
-      st.busy = false;
+      for (Request& rq : sl.reqs) {
+        ServerSet& st = *s->sets[rq.set];
+        lk.unlock();
+        const vrt_status status = vrt_sync(st.grid);  // the frame's device status
+        uint64_t b = 0;
+        vrt_grid_device_bytes(st.grid, &b);
+        lk.lock();
+        s->resident_bytes += b - st.bytes;  // lazily sized buffers may have grown
+        st.bytes = b;
+        st.busy = false;
+        finish(s, rq, status, sl.t_done);
+      }
+      sl.reqs.clear();
       sl.busy = false;
       sl.done.store(false);
-      finish(s, sl.req, status, sl.t_done);
     }
     trim(s, lk);
     // (2) issue: the oldest queued request of each idle set, while slots are free
@@ -286,6 +456,10 @@ void scheduler(vrt_server s) {
       for (auto& slp : s->slots)
         if (!slp->busy) { free_slot = slp.get(); break; }
       if (!free_slot) break;
+      if (s->small_segments > 0 && issue_small_batch(s, lk, *free_slot, blocked)) {
+        issued = true;
+        continue;
+      }
       // the first request that is the oldest of its set, whose set is idle and not blocked
       std::vector<char> seen(s->sets.size(), 0);
       size_t pick = s->pending.size();
@@ -314,10 +488,11 @@ void scheduler(vrt_server s) {
       }
       if (ok) {
         rq.t_issue = Clock::now();
-        free_slot->req = rq;
+        free_slot->reqs.assign(1, rq);
         lk.unlock();
-        r = issue(s, *free_slot, free_slot->req);
+        r = issue(s, *free_slot, free_slot->reqs[0]);
         lk.lock();
+        if (r != VRT_OK) free_slot->reqs.clear();
       }
       if (r != VRT_OK) {
         // Part of the frame may already be on the slot's stream (the update
@@ -351,6 +526,7 @@ vrt_status vrt_server_create(const vrt_server_desc* desc, vrt_server* out) {
   if (!out || !desc) return sfail(nullptr, VRT_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   if (desc->max_inflight < 0) return sfail(nullptr, VRT_ERR_INVALID_ARG, "max_inflight must be >= 0");
+  if (desc->max_batch < 0) return sfail(nullptr, VRT_ERR_INVALID_ARG, "max_batch must be >= 0");
   vrt_server s = new (std::nothrow) vrt_server_s();
   if (!s) return sfail(nullptr, VRT_ERR_OOM, "host allocation failed");
   s->device = desc->device;
@@ -363,6 +539,8 @@ vrt_status vrt_server_create(const vrt_server_desc* desc, vrt_server* out) {
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   s->budget = desc->hbm_budget ? desc->hbm_budget : (uint64_t)(0.8 * (double)fr);
+  s->small_segments = desc->small_segments;
+  s->max_batch = desc->max_batch == 0 ? 16 : std::min(64, std::max(2, desc->max_batch));
   const int slots = desc->max_inflight ? desc->max_inflight : 4;
   for (int i = 0; i < slots; ++i) {
     auto sl = std::make_unique<Slot>();
@@ -498,6 +676,8 @@ vrt_status vrt_server_get_stats(vrt_server s, vrt_server_stats* out) {
   for (auto& sl : s->slots) inflight += sl->busy ? 1 : 0;
   out->inflight = inflight;
   out->resident_sets = s->resident_sets;
+  out->batches = s->batches;
+  out->batched_frames = s->batched_frames;
   return VRT_OK;
 }
 
@@ -514,7 +694,12 @@ vrt_status vrt_server_destroy(vrt_server s) {
   cudaSetDevice(s->device);
   for (auto& st : s->sets)
     if (st->grid) vrt_destroy(st->grid);
-  for (auto& sl : s->slots) cudaStreamDestroy(sl->stream);
+  for (auto& sl : s->slots) {
+    cudaStreamDestroy(sl->stream);
+    for (cudaStream_t b : sl->branch) cudaStreamDestroy(b);
+    for (cudaEvent_t e : sl->join) cudaEventDestroy(e);
+    if (sl->fork) cudaEventDestroy(sl->fork);
+  }
   for (float* p : s->pinned_all) cudaFreeHost(p);
   cudaSetDevice(prev);
   delete s;

@@ -831,16 +831,18 @@ __device__ __forceinline__ void finish(const TraceArgs& A, const Ray& R, bool va
   if (A.first_t) A.first_t[R.pix] = R.first_t;
 }
 
-// Transparent main trace: each warp owns one fixed tile 4 pixels wide and 8
-// tall (a block 2x2 tiles), and its lanes write their pixels together at the
-// end. Measured faster than persistent refilling here, since the tile's rays
-// share lists (and slightly faster than 8x4 or 16x2 tiles).
-template <bool OPAQUE, bool COUNT, bool KEY16>
+// Transparent main trace: each warp owns one fixed tile of 32 pixels, TW wide
+// and 32 / TW tall (a block 2x2 tiles), and its lanes write their pixels
+// together at the end. Measured faster than persistent refilling here, since
+// the tile's rays share lists. The tile shape is a tuned parameter (default
+// 4 x 8, measured slightly faster than 8 x 4 or 16 x 2 on the bundles frame).
+template <bool OPAQUE, bool COUNT, bool KEY16, int TW>
 __global__ void __launch_bounds__(kTraceThreads) k_trace_tile(TraceArgs A) {
+  constexpr int TH = 32 / TW;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int px = blockIdx.x * 8 + (warp & 1) * 4 + (lane & 3);
-  const int py = blockIdx.y * 16 + (warp >> 1) * 8 + (lane >> 2);
+  const int px = blockIdx.x * (2 * TW) + (warp & 1) * TW + (lane % TW);
+  const int py = blockIdx.y * (2 * TH) + (warp >> 1) * TH + (lane / TW);
   const bool valid = px < A.cam.width && py < A.cam.height;
   Ray R;
   R.cyc[0] = R.cyc[1] = R.cyc[2] = R.cyc[3] = 0;
@@ -997,8 +999,18 @@ int persistent_blocks(size_t smem) {
 template <bool OPAQUE, bool COUNT, bool KEY16>
 void launch_one(const TraceArgs& a, size_t smem, cudaStream_t s) {
   if (!OPAQUE && !a.pix_list) {
-    const dim3 grid((a.cam.width + 7) / 8, (a.cam.height + 15) / 16);
-    k_trace_tile<OPAQUE, COUNT, KEY16><<<grid, kTraceThreads, smem, s>>>(a);
+    // the instrumented and 16+16-key traces use the default tile
+    const int tw = (COUNT || KEY16) ? 4 : a.tile_w;
+    const int th = 32 / tw;
+    const dim3 grid((a.cam.width + 2 * tw - 1) / (2 * tw), (a.cam.height + 2 * th - 1) / (2 * th));
+    if constexpr (COUNT || KEY16) {
+      k_trace_tile<OPAQUE, COUNT, KEY16, 4><<<grid, kTraceThreads, smem, s>>>(a);
+    } else {
+      if (tw == 2) k_trace_tile<OPAQUE, COUNT, KEY16, 2><<<grid, kTraceThreads, smem, s>>>(a);
+      else if (tw == 8) k_trace_tile<OPAQUE, COUNT, KEY16, 8><<<grid, kTraceThreads, smem, s>>>(a);
+      else if (tw == 16) k_trace_tile<OPAQUE, COUNT, KEY16, 16><<<grid, kTraceThreads, smem, s>>>(a);
+      else k_trace_tile<OPAQUE, COUNT, KEY16, 4><<<grid, kTraceThreads, smem, s>>>(a);
+    }
   } else {
     k_trace<OPAQUE, COUNT, KEY16><<<persistent_blocks<OPAQUE, COUNT, KEY16>(smem), kTraceThreads, smem, s>>>(a);
   }

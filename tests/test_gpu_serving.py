@@ -111,6 +111,29 @@ def test_served_frames_equal_frames_alone():
     _assert_equal(served, alone)
     assert stats["completed"] == len(reqs) and stats["evictions"] == 0
     assert stats["resident_sets"] == len(sets)
+    assert stats["batches"] == 0
+
+
+def test_batched_small_set_frames_equal_frames_alone():
+    """With small_segments = 100000, three of the four sets are small: their
+    pending frames go out in batches (one CUDA graph launch per batch)."""
+    sets = _sets()
+    reqs = _requests(sets, 40, seed=8)
+    alone = _plain(sets, reqs)
+    served, res, stats = _served(sets, reqs, max_inflight=3, small_segments=100_000)
+    _assert_equal(served, alone)
+    assert stats["batches"] > 0 and stats["batched_frames"] >= 2 * stats["batches"]
+
+
+def test_small_set_batches_of_two_equal_frames_alone():
+    """Batches capped at two frames, one slot: every batch waits for the one
+    before it, and frames of the same set stay in submission order."""
+    sets = _sets()[:3]
+    reqs = _requests(sets, 18, seed=9)
+    alone = _plain(sets, reqs)
+    served, res, stats = _served(sets, reqs, max_inflight=1, small_segments=100_000, max_batch=2)
+    _assert_equal(served, alone)
+    assert stats["batches"] > 0
 
 
 def test_served_frames_with_evictions_equal_frames_alone():
@@ -252,3 +275,28 @@ def test_tune_grid_side():
     assert best in (32, 64, 128)
     assert all(np.isfinite(v) and v > 0 for v in ms.values())
     assert ms[best] == min(ms.values())
+
+
+def test_tune_shapes_and_tile_widths_give_the_same_image():
+    """The tuner measures every (grid side, trace tile) pair; the tile shape of
+    the transparent trace changes speed only: images are bitwise equal."""
+    ls = _sets()[1]
+    cam = _camera(np.random.default_rng(5), ls.n, 96, 64)
+    (side, tile), ms = vrt.tune_shapes(ls.xyz, ls.offsets, ls.n, ls.radius, cam, [32, 64],
+                                       tiles=(2, 4, 8, 16), alpha=0.4, cull_on=1)
+    assert len(ms) == 8 and all(np.isfinite(v) and v > 0 for v in ms.values())
+    assert ms[(side, tile)] == min(ms.values())
+    r = vrt.Renderer(ls.n, ls.radius)
+    r.upload(ls.xyz, ls.offsets)
+    imgs = []
+    for tw in (4, 2, 8, 16):
+        vrt.set_option(r.h, vrt.OPT_TRACE_TILE, tw)
+        rgba, fid, ft = r.frame(cam, alpha=0.4, cull_on=1)
+        vrt.sync(r.h)
+        imgs.append((rgba.cpu().numpy().copy(), fid.cpu().numpy().copy(), ft.cpu().numpy().copy()))
+    with pytest.raises(vrt.VrtError):
+        vrt.set_option(r.h, vrt.OPT_TRACE_TILE, 3)
+    r.close()
+    for img in imgs[1:]:
+        for a, b in zip(imgs[0], img):
+            assert np.array_equal(a, b)
