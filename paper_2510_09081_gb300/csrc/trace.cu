@@ -216,7 +216,14 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
     if (COUNT) ++R.n_steps;
     const uint32_t bidx = ((uint32_t)(R.vz >> 2) << (2 * A.g.log2nb)) |
                           ((uint32_t)(R.vy >> 2) << A.g.log2nb) | (uint32_t)(R.vx >> 2);
+    const uint32_t idx = brick_index(R.vx, R.vy, R.vz, A.g.log2nb);
+    // the step's loads are independent: issue them together (one latency, not
+    // up to four in sequence); the word, mark and list end go unused in an
+    // empty brick
     const int kd = __ldg(&A.g.bdist[bidx]);
+    const uint32_t wv = __ldg(&A.g.word[idx]);
+    const uint32_t vb = __ldg(&A.g.vis[idx >> 5]);
+    const uint32_t cv = __ldg(&A.g.cur[idx]);
     if (kd > 0) {
       // cross the cube of empty bricks within kd - 1 of this one: low corner
       // (bx, by, bz), side w voxels
@@ -247,8 +254,7 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
     const float ty = exit_t(R.sy, R.vy, R.vy + 1, R.ooi.y, R.inv.y);
     const float tz = exit_t(R.sz, R.vz, R.vz + 1, R.ooi.z, R.inv.z);
     const float texit = fminf(tx, fminf(ty, tz));
-    const uint32_t idx = brick_index(R.vx, R.vy, R.vz, A.g.log2nb);
-    const uint32_t cnt = __ldg(&A.g.word[idx]) & 0xffffu;
+    const uint32_t cnt = wv & 0xffffu;
     if (COUNT) touch(A.touch_vox, idx);
     const float tin = R.tcur;
     // step past this voxel before returning, so the next call resumes after it
@@ -265,7 +271,7 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
       inside = R.vz >= 0 && R.vz < n;
     }
     if (cnt) {
-      if (!bit_at(A.g.vis, idx)) {
+      if (!((vb >> (idx & 31)) & 1u)) {
         // culled voxel on the ray: queue it, march on as if it were empty; at
         // the first one, keep the ray's state for the re-trace to resume from
         if (R.n_queued == 0 && A.resume) {
@@ -284,7 +290,7 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
         if (++R.n_queued >= A.max_queue) return false;
       } else {
         // a list past the capacity (reported as overflow) is read only up to it
-        const uint32_t end0 = __ldg(&A.g.cur[idx]);
+        const uint32_t end0 = cv;
         if (end0 < cnt) {
           set_err(A.g.st, kErrBounds);
           return false;

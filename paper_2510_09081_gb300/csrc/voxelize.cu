@@ -153,14 +153,14 @@ __device__ __forceinline__ bool decode_candidate(const PackedWalk& p, int n, uin
   // these small counts, so truncation gives the exact quotient
   int slab, rem;
   if (bits & (1u << 29)) {  // exact: the slab whose cumulative range holds q
-    const uint32_t pre[4] = {p.w4.x, p.w4.y, p.w4.z, p.w4.w};
-    slab = 0;
-    uint32_t base = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t v = (pre[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-      if (v <= q) { slab = k + 1; base = v; }
-    }
+    // the number of cumulative counts <= q (non-decreasing, 16 bits each, two
+    // per word; q < 65535), by packed half-word comparisons
+    const uint32_t qq = q * 0x00010001u;
+    slab = (__popc(__vcmpleu2(p.w4.x, qq)) + __popc(__vcmpleu2(p.w4.y, qq)) +
+            __popc(__vcmpleu2(p.w4.z, qq)) + __popc(__vcmpleu2(p.w4.w, qq))) >> 4;
+    const int s1 = slab - 1;
+    const uint32_t word = s1 < 2 ? p.w4.x : (s1 < 4 ? p.w4.y : (s1 < 6 ? p.w4.z : p.w4.w));
+    const uint32_t base = slab ? (word >> (16 * (s1 & 1))) & 0xffffu : 0u;
     rem = (int)(q - base);
   } else {
     slab = (int)(((float)q + 0.5f) * p.w3.x);
@@ -170,7 +170,9 @@ __device__ __forceinline__ bool decode_candidate(const PackedWalk& p, int n, uin
   int j0, j1, l0, l1;
   slab_box(am, a1, a2, p.w0.w, p.w1.w, p.w2.x, p.w2.y, p.w2.z, p.w2.w, n, c, j0, j1, l0, l1);
   const int w2 = (bits & (1u << 29)) ? l1 - l0 + 1 : W2;
-  const float inv_w2 = (bits & (1u << 29)) ? __frcp_rn((float)w2) : p.w3.y;
+  // an approximate reciprocal suffices: (rem + 1/2) / w2 lies at least 1/(2 w2)
+  // from an integer and rem < 256
+  const float inv_w2 = (bits & (1u << 29)) ? __fdividef(1.0f, (float)w2) : p.w3.y;
   const int dj = (int)(((float)rem + 0.5f) * inv_w2);
   const int dl = rem - dj * w2;
   const int j = j0 + dj, l = l0 + dl;
