@@ -179,8 +179,9 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
 vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_vertices,
                                const float* xyz, int32_t stride, int32_t on_device);
 
-/* Ingest (snap, flags, clip normals) and voxelization pass 1 (Sec. 3.1, Alg. 1
- * walk, Alg. 3 occupancy): for every segment and every voxel within the list
+/* Ingest (snap, flags, clip normals) of the vertices uploaded or updated since
+ * the last vrt_voxelize (and their polyline neighbours), and voxelization pass 1
+ * (Sec. 3.1, Alg. 1 walk, Alg. 3 occupancy): for every segment and every voxel within the list
  * radius of it (r + 2^-9, decided exactly), one 32-bit atomic add of
  * (occupancy code << 16) | 1 into the voxel's packed word. */
 vrt_status vrt_voxelize(vrt_grid g);

@@ -2,6 +2,7 @@
 // status. Every step of the frame runs in the kernels of this library; this
 // file only validates arguments, allocates, and issues launches and copies on
 // the grid's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -25,6 +26,9 @@ struct vrt_grid_s {
   cudaStream_t stream = nullptr;
   // vertices
   long long V = 0, P = 0, V_alloc = 0;
+  // vertices uploaded or updated since the last ingest, with their polyline
+  // neighbours: [dirty_lo, dirty_hi), empty when dirty_lo >= dirty_hi
+  long long dirty_lo = 0, dirty_hi = 0;
   float* raw = nullptr;
   uint8_t* flags = nullptr;
   float4* pos = nullptr;
@@ -590,6 +594,8 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
   }
   g->stage = 1;
   g->mips_valid = false;
+  g->dirty_lo = 0;
+  g->dirty_hi = V;
   return VRT_OK;
 }
 
@@ -605,6 +611,17 @@ vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_verti
   // device input alike; vrt_sync reports a bad one
   vrt_status s = copy_vertices(g, first_vertex, n_vertices, xyz, stride, on_device);
   if (s != VRT_OK) return s;
+  if (n_vertices > 0) {  // these vertices and the neighbours whose clip normals they enter
+    const long long lo = std::max<long long>(0, first_vertex - 1);
+    const long long hi = std::min<long long>(g->V, first_vertex + n_vertices + 1);
+    if (g->dirty_lo >= g->dirty_hi) {
+      g->dirty_lo = lo;
+      g->dirty_hi = hi;
+    } else {
+      g->dirty_lo = std::min(g->dirty_lo, lo);
+      g->dirty_hi = std::max(g->dirty_hi, hi);
+    }
+  }
   g->stage = 1;
   g->mips_valid = false;
   return VRT_OK;
@@ -620,7 +637,10 @@ vrt_status vrt_voxelize(vrt_grid g) {
   VRT_CUDA(g, cudaMemsetAsync(g->word, 0, nv * 4, g->stream));
   for (int i = 0; i < VRT_N_STAGES; ++i) g->ev_used[i] = false;
   stage_mark(g, ST_INGEST, 0);
-  g->launches += launch_ingest(g->raw, g->flags, g->V, g->pos, g->nrm, g->st, g->stream);
+  // the vertices that changed since the last ingest (all of them after an upload)
+  g->launches += launch_ingest(g->raw, g->flags, g->dirty_lo, g->dirty_hi, g->pos, g->nrm, g->st,
+                               g->stream);
+  g->dirty_lo = g->dirty_hi = 0;
   stage_mark(g, ST_INGEST, 1);
   stage_mark(g, ST_PASS1, 0);
   g->launches += launch_pass1(g->pos, g->nrm, g->order, g->V, gdev(g), g->stream);

@@ -14,12 +14,14 @@ __device__ __forceinline__ float snap(float x, bool& bad) {
   return rintf(x * kUnits) * (1.0f / kUnits);
 }
 
+// Vertices [lo, hi): the ones uploaded or updated since the last ingest and
+// their polyline neighbours (whose clip normals they enter).
 __global__ void __launch_bounds__(256) k_ingest(const float* __restrict__ raw,
-                                                const uint8_t* __restrict__ flags, long long V,
-                                                float4* __restrict__ pos, float4* __restrict__ nrm,
-                                                DevStatus* st) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V) return;
+                                                const uint8_t* __restrict__ flags, long long lo,
+                                                long long hi, float4* __restrict__ pos,
+                                                float4* __restrict__ nrm, DevStatus* st) {
+  const long long i = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
   bool bad = false;
   const float x = snap(raw[3 * i], bad), y = snap(raw[3 * i + 1], bad), z = snap(raw[3 * i + 2], bad);
   uint32_t fl = flags[i];
@@ -41,11 +43,11 @@ __global__ void __launch_bounds__(256) k_ingest(const float* __restrict__ raw,
   nrm[i] = n;
 }
 
-int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,
-                   DevStatus* st, cudaStream_t s) {
-  if (V <= 0) return 0;
+int launch_ingest(const float* raw, const uint8_t* flags, long long lo, long long hi, float4* pos,
+                  float4* nrm, DevStatus* st, cudaStream_t s) {
+  if (hi <= lo) return 0;
   const int T = 256;
-  k_ingest<<<(unsigned)((V + T - 1) / T), T, 0, s>>>(raw, flags, V, pos, nrm, st);
+  k_ingest<<<(unsigned)((hi - lo + T - 1) / T), T, 0, s>>>(raw, flags, lo, hi, pos, nrm, st);
   return 1;
 }
 

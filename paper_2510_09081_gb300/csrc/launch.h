@@ -83,8 +83,9 @@ int launch_shade(const ShadeArgs& a, cudaStream_t s);
 // Voxels next to the voxels a repair round listed, not yet shaded this frame.
 int launch_shade_repair(const ShadeArgs& a, cudaStream_t s);
 
-int launch_ingest(const float* raw, const uint8_t* flags, long long V, float4* pos, float4* nrm,
-                   DevStatus* st, cudaStream_t s);
+// Ingest of vertices [lo, hi) (nothing when hi <= lo).
+int launch_ingest(const float* raw, const uint8_t* flags, long long lo, long long hi, float4* pos,
+                  float4* nrm, DevStatus* st, cudaStream_t s);
 // Pass 1 over the segments in the order `order` (V vertex indices, each
 // polyline's vertices consecutive; a polyline's last vertex starts no
 // segment), or in index order when `order` is null.

@@ -256,6 +256,25 @@ def test_abc_fullsize_sampled_pixels_without_ao(abc_frame):
     assert res["hits"] >= 100, res
 
 
+def test_abc_fullsize_ao_pixels_against_oracle(abc_frame):
+    """Cone AO at full size: the 512^3 pyramid of all 31M segments, whose cones
+    sample levels 1 to 5, on 256 sampled pixels against the oracle's full list
+    build and fp64 pyramid (about a minute of oracle time on the host)."""
+    cam, o = abc_frame["cam"], abc_frame["oracle"]
+    pix = np.random.default_rng(10).choice(cam.width * cam.height, 256, replace=False)
+    ref = o.render_pixels(cam, pix, alpha=1.0, ao_cones=6)
+    rgba, fid, ft = abc_frame["ao"]
+    res = compare_image(rgba[pix], fid[pix], ft[pix], ref)
+    assert res["col_bad"] == 0 and res["id_bad"] == 0, res
+    assert res["exempt_colour"] <= 0.01 * res["n"] and res["exempt_id"] <= 0.01 * res["n"], res
+    assert res["max_t_rel"] < 2e-4, res
+    assert res["hits"] >= 200, res
+    # AO is partial at most of these hits (the test is not trivially AO = 1)
+    plain = abc_frame["plain"][0][pix]
+    hit = fid[pix] >= 0
+    assert (rgba[pix][hit, :3].sum(1) < 0.95 * plain[hit, :3].sum(1)).mean() > 0.2
+
+
 def test_abc_fullsize_ao_properties(abc_frame):
     rgba_ao, fid_ao, ft_ao = abc_frame["ao"]
     rgba, fid, ft = abc_frame["plain"]

@@ -344,8 +344,17 @@ def test_update_vertices_equals_fresh_upload():
     vrt.voxelize(r.h)
     vrt.sync(r.h)
     w_upd = vrt.read_grid(r.h, 64)
+    # only the updated vertices and their neighbours are ingested again: the
+    # frame equals one from a fresh upload of the new vertices, bitwise
+    cam = _persp_cam()
+    img_upd = gpu_image(r, cam, alpha=0.3, voxelize=False)
     r.close()
     fresh = LineSet(xyz=new, offsets=ls.offsets, n=64, radius=ls.radius)
+    r2 = gpu_grid(fresh)
+    img_fresh = gpu_image(r2, cam, alpha=0.3)
+    r2.close()
+    for a, b in zip(img_upd, img_fresh):
+        assert np.array_equal(a, b)
     L = oracle.Oracle.from_lineset(fresh).lists()
     check_words(w_upd, L)
 
