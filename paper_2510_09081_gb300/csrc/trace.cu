@@ -55,6 +55,7 @@ constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept
 // kRayKeys (vrt_internal.cuh): hit slots per transparent ray on the shared-entry
 // path, 40 KB of shared memory per block; A.ray_keys <= kRayKeys of them are used
 constexpr int kTraceThreads = 128;
+constexpr int kStepRound = 1;             // tile trace: DDA steps a walking lane takes per round
 
 __device__ __forceinline__ bool bit_at(const uint32_t* bits, uint32_t i) {
   return (bits[i >> 5] >> (i & 31)) & 1u;
@@ -205,14 +206,15 @@ __device__ __forceinline__ float exit_t(int s, int lo, int hi, float ooi, float 
   return s != 0 ? fmaf((float)(s > 0 ? hi : lo), inv, -ooi) : __int_as_float(0x7f800000);
 }
 
-// Step the lane's ray to its next voxel that has a list; returns false when the
-// ray leaves the grid (or queues too many culled voxels).
+// Step the lane's ray toward its next voxel that has a list, at most `budget`
+// steps: 1 when it reached one (pending), 0 when the ray leaves the grid (or
+// queues too many culled voxels), -1 when the budget ran out first. Every step
+// moves the ray forward through the grid, so its walk ends.
 template <bool COUNT>
-__device__ bool advance(const TraceArgs& A, Ray& R) {
+__device__ int advance(const TraceArgs& A, Ray& R, int budget) {
   const int n = A.g.n;
-  const int max_steps = 3 * n + 16;
-  for (int it = 0; it < max_steps; ++it) {
-    if (R.tcur > R.t1) return false;
+  for (int it = 0; it < budget; ++it) {
+    if (R.tcur > R.t1) return 0;
     if (COUNT) ++R.n_steps;
     const uint32_t bidx = ((uint32_t)(R.vz >> 2) << (2 * A.g.log2nb)) |
                           ((uint32_t)(R.vy >> 2) << A.g.log2nb) | (uint32_t)(R.vx >> 2);
@@ -233,19 +235,19 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
       const float ty = exit_t(R.sy, by, by + w, R.ooi.y, R.inv.y);
       const float tz = exit_t(R.sz, bz, bz + w, R.ooi.z, R.inv.z);
       const float tb = fminf(tx, fminf(ty, tz));
-      if (tb > R.t1) return false;
+      if (tb > R.t1) return 0;
       const int cx = min(min(bx + w, n) - 1, max(max(bx, 0), (int)floorf(fmaf(tb, R.d.x, R.o.x))));
       const int cy = min(min(by + w, n) - 1, max(max(by, 0), (int)floorf(fmaf(tb, R.d.y, R.o.y))));
       const int cz = min(min(bz + w, n) - 1, max(max(bz, 0), (int)floorf(fmaf(tb, R.d.z, R.o.z))));
       if (tb == tx) {
         R.vx = R.sx > 0 ? bx + w : bx - 1; R.vy = cy; R.vz = cz;
-        if (R.vx < 0 || R.vx >= n) return false;
+        if (R.vx < 0 || R.vx >= n) return 0;
       } else if (tb == ty) {
         R.vy = R.sy > 0 ? by + w : by - 1; R.vx = cx; R.vz = cz;
-        if (R.vy < 0 || R.vy >= n) return false;
+        if (R.vy < 0 || R.vy >= n) return 0;
       } else {
         R.vz = R.sz > 0 ? bz + w : bz - 1; R.vx = cx; R.vy = cy;
-        if (R.vz < 0 || R.vz >= n) return false;
+        if (R.vz < 0 || R.vz >= n) return 0;
       }
       R.tcur = fmaxf(R.tcur, tb);
       continue;
@@ -287,13 +289,13 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
           else set_err(A.g.st, kErrOverflow);
         }
         R.missed = true;
-        if (++R.n_queued >= A.max_queue) return false;
+        if (++R.n_queued >= A.max_queue) return 0;
       } else {
         // a list past the capacity (reported as overflow) is read only up to it
         const uint32_t end0 = cv;
         if (end0 < cnt) {
           set_err(A.g.st, kErrBounds);
-          return false;
+          return 0;
         }
         const uint32_t end = (unsigned long long)end0 > A.g.list_cap ? (uint32_t)A.g.list_cap : end0;
         R.beg = end0 - cnt < end ? end0 - cnt : end;
@@ -301,12 +303,12 @@ __device__ bool advance(const TraceArgs& A, Ray& R) {
         R.vt0 = tin;
         R.vt1 = texit;
         if (!inside) R.t1 = -1.0f;  // this was the last voxel; stop after it
-        return true;
+        return 1;
       }
     }
-    if (!inside) return false;
+    if (!inside) return 0;
   }
-  return false;
+  return -1;  // budget used up, ray still on its way
 }
 
 __device__ void init_ray(const TraceArgs& A, Ray& R, int px, int py, bool valid) {
@@ -773,10 +775,20 @@ __device__ void trace_warp(const TraceArgs& A, Ray& R) {
   long long t = COUNT ? clock64() : 0;
   for (;;) {
     if (R.active && !R.pending) {
-      R.pending = advance<COUNT>(A, R);
-      if (!R.pending) R.active = false;
+      const int rc = advance<COUNT>(A, R, kStepRound);
+      R.pending = rc == 1;
+      if (rc == 0) R.active = false;
     }
-    if (!__any_sync(FULL, R.pending)) break;
+    // The warp steps its walking rays one voxel (or empty cube) per round and
+    // processes the waiting lists once a quarter of the rays still in flight
+    // wait at one (or none can step on). Stepping each ray to its next list in
+    // one go left most lanes idle while the longest walk went on (5.9 of 32
+    // lanes active per instruction on a sparse 512^3 set): bounded rounds cut
+    // that trace by 41-47% and the dense bundles' by 4%.
+    const unsigned pend = __ballot_sync(FULL, R.pending);
+    const unsigned walk = __ballot_sync(FULL, R.active && !R.pending);
+    if (!pend && !walk) break;
+    if (walk && 4 * __popc(pend) < __popc(pend | walk)) continue;
     lap<COUNT>(R.cyc[0], t);
     process_flat<OPAQUE, COUNT, KEY16>(A, R);
     lap<COUNT>(R.cyc[1], t);
@@ -937,7 +949,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(TraceArgs A) {
       continue;
     }
     if (has && R.active && !R.pending) {
-      R.pending = advance<COUNT>(A, R);
+      R.pending = advance<COUNT>(A, R, 3 * A.g.n + 16) == 1;
       if (!R.pending) R.active = false;
     }
     lap<COUNT>(R.cyc[0], tclk);
