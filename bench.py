@@ -83,6 +83,28 @@ def make_workload(name, scale=1.0):
                     desc=("ABC-flow lines: 1M x 32 vertices (31M segments), grid 512^3, r 0.25, "
                           "1920x1080 perspective from the centre, opaque, 6-cone AO, culling on, "
                           "every vertex moves per frame"))
+    if name == "sparse":
+        # the serving mix's heaviest request: its largest set (random walks of
+        # 20-200 vertices, 512^3) seen at 4K and opacity 0.2
+        rng = np.random.default_rng(20251013)
+        sizes = np.exp(rng.uniform(np.log(1e4), np.log(5e6), 64)).astype(np.int64)
+        k = int(np.argmax(sizes))
+        ls = G.walk_set(int(round(int(sizes[k]) * scale)), 512, radius=0.4, seed=20251100 + 7 * k)
+        c = 256.0
+        cam = G.Camera(width=3840, height=2160, ortho=0, eye=(c + 1.7 * 512, c, c + 0.5 * 512),
+                       target=(c, c, c), up=(0.0, 0.0, 1.0), fovy_deg=45.0)
+        rng2 = np.random.default_rng(11)
+
+        def upd(f):
+            cnt = ls.n_vertices // 50
+            first = (f * cnt) % (ls.n_vertices - cnt)
+            return first, np.clip(ls.xyz[first:first + cnt] + rng2.normal(0, 0.05, (cnt, 3)), 1.0,
+                                  511.0).astype(np.float32)
+        return dict(ls=ls, cam=cam, update=upd, alpha=0.2, ao=0, cull=2,
+                    desc=("sparse random walks: the serving mix's largest set (%d segments, "
+                          "20-200 vertices per walk), grid 512^3, r 0.4, 3840x2160 perspective, "
+                          "alpha 0.2 ordered compositing, automatic culling, 2%% of vertices "
+                          "moved per frame" % ls.n_segments))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -723,7 +745,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc", "serve"])
+    ap.add_argument("--workload", default="bundles", choices=["bundles", "walks", "abc", "sparse", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hit-key", choices=("depth-id", "16+16"), default="depth-id",
                     help="order of a ray's hits within a voxel (16+16: the paper's 32-bit key)")
