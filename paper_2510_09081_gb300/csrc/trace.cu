@@ -113,7 +113,7 @@ __device__ __forceinline__ float3 tangent_colour(const TraceArgs& A, uint32_t id
   const float3 dv = b - a;
   const float l2 = dot3(dv, dv);
   if (!(l2 > 0.0f)) return make_float3(1.0f, 1.0f, 1.0f);
-  const float il = 1.0f / sqrtf(l2);
+  const float il = rsqrtf(l2);  // the hardware's approximate reciprocal square root
   return make_float3(fabsf(dv.x) * il, fabsf(dv.y) * il, fabsf(dv.z) * il);
 }
 

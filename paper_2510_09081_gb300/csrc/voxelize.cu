@@ -22,8 +22,10 @@
 // Pass 1 adds (occupancy code << 16) | 1 to the voxel's packed word with a
 // 32-bit atomic (Sec. 3.1) -- on grids of side 512 and more one per distinct
 // voxel of a warp step, the increments of lanes that share the voxel summed
-// first -- and appends the fragment as an 8-byte record (voxel << 32 |
-// segment), warp-aggregated. The paper re-voxelizes in its
+// first -- and writes the fragment as an 8-byte record (voxel << 32 |
+// segment). A block takes record slots for all its walks' candidates with one
+// atomic; each warp writes its fragments at the start of its share and marks
+// the rest (candidates that were not kept) kNoRecord. The paper re-voxelizes in its
 // second pass to save memory; with the records in HBM the second pass is a
 // streaming scatter instead: for every record whose voxel received a list,
 // bump the voxel's cursor and write the segment id (Sec. 3.3).
@@ -40,11 +42,14 @@ struct Walk {
   float inv_w12, inv_w2;  // reciprocals of W1 * W2 and W2 for the uniform decode
   int m, c0, W1, W2;
   bool exact;             // candidates are exactly the slab boxes' voxels
+  bool boxed;             // exact, with at most kBoxedSlabs slabs: boxes kept
   uint32_t pre[4];        // exact: 16-bit cumulative counts after slabs 0..7
+  uint32_t box[6];        // boxed: slab k's box, j0 | l0 << 10 | (l1 - l0 + 1) << 20
   uint32_t n;             // candidates
 };
 
 constexpr int kExactSlabs = 9;  // slabs whose boxes the exact decode indexes
+constexpr int kBoxedSlabs = 6;  // slabs whose boxes the packed walk can hold
 
 // Minor-axis voxel ranges of slab c (clamped to the grid): the axis line
 // a_k + (x - a_m) s_k over the slab's part of [lo_m, hi_m], widened by rho_k.
@@ -97,6 +102,9 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
     W1 = max(W1, j1 - j0 + 1);
     W2 = max(W2, l1 - l0 + 1);
     total += (uint32_t)(max(0, j1 - j0 + 1) * max(0, l1 - l0 + 1));
+    if (k < kBoxedSlabs)
+      w.box[k] = ((uint32_t)j0 & 1023u) | (((uint32_t)l0 & 1023u) << 10) |
+                 ((uint32_t)max(1, l1 - l0 + 1) << 20);
     if (k < 8) {  // cumulative count after slab k
       const uint32_t v = min(total, 0xffffu);
       w.pre[k >> 1] = (w.pre[k >> 1] & ~(0xffffu << (16 * (k & 1)))) | (v << (16 * (k & 1)));
@@ -112,6 +120,7 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
   w.W1 = W1;
   w.W2 = W2;
   w.exact = slabs > 0 && slabs <= kExactSlabs && total < 0xffffu;
+  w.boxed = w.exact && slabs <= kBoxedSlabs;
   w.n = slabs <= 0 ? 0u : (w.exact ? total : (uint32_t)slabs * (uint32_t)(W1 * W2));
   w.inv_w12 = 1.0f / (float)(W1 * W2);
   w.inv_w2 = 1.0f / (float)W2;
@@ -121,7 +130,10 @@ __device__ __forceinline__ void walk_setup(float3 a, float3 b, const GridDev& g,
 //   w0 = (a, s1), w1 = (b, s2), w2 = (rho1, rho2, lo_m, hi_m),
 //   w3 = (1 / (W1 W2), 1 / W2, bits, first candidate number of the warp),
 //   w4 = cumulative counts after slabs 0..7, 16 bits each (exact decode),
-//   bits = m | c0 << 2 | W1 << 11 | W2 << 19 | clip flags << 27 | exact << 29.
+//   bits = m | c0 << 2 | W1 << 11 | W2 << 19 | clip flags << 27 | exact << 29
+//          | boxed << 30.
+// A boxed walk keeps its slab boxes, as walk_setup found them, where the
+// uniform decode's fields would be: slabs 0-3 in w2, slabs 4-5 in w3.x, w3.y.
 // W1, W2 <= 2 + |s_k| + 2 rho_k < 16 since radius <= 4, and c0 < 512.
 struct PackedWalk {
   float4 w0, w1, w2, w3;
@@ -132,10 +144,18 @@ __device__ __forceinline__ PackedWalk pack_walk(const Walk& w, uint32_t clip, ui
   PackedWalk p;
   p.w0 = make_float4(w.a.x, w.a.y, w.a.z, w.s1);
   p.w1 = make_float4(w.b.x, w.b.y, w.b.z, w.s2);
-  p.w2 = make_float4(w.rho1, w.rho2, w.lo_m, w.hi_m);
   const uint32_t bits = (uint32_t)w.m | ((uint32_t)w.c0 << 2) | ((uint32_t)w.W1 << 11) |
-                        ((uint32_t)w.W2 << 19) | (clip << 27) | ((uint32_t)w.exact << 29);
-  p.w3 = make_float4(w.inv_w12, w.inv_w2, __uint_as_float(bits), __uint_as_float(first));
+                        ((uint32_t)w.W2 << 19) | (clip << 27) | ((uint32_t)w.exact << 29) |
+                        ((uint32_t)w.boxed << 30);
+  if (w.boxed) {
+    p.w2 = make_float4(__uint_as_float(w.box[0]), __uint_as_float(w.box[1]),
+                       __uint_as_float(w.box[2]), __uint_as_float(w.box[3]));
+    p.w3 = make_float4(__uint_as_float(w.box[4]), __uint_as_float(w.box[5]), __uint_as_float(bits),
+                       __uint_as_float(first));
+  } else {
+    p.w2 = make_float4(w.rho1, w.rho2, w.lo_m, w.hi_m);
+    p.w3 = make_float4(w.inv_w12, w.inv_w2, __uint_as_float(bits), __uint_as_float(first));
+  }
   p.w4 = make_uint4(w.pre[0], w.pre[1], w.pre[2], w.pre[3]);
   return p;
 }
@@ -167,6 +187,20 @@ __device__ __forceinline__ bool decode_candidate(const PackedWalk& p, int n, uin
     rem = (int)q - slab * (W1 * W2);
   }
   const int c = c0 + slab;
+  if (bits & (1u << 30)) {  // boxed: the slab's box as walk_setup found it; q lies inside it
+    const uint32_t bx = __float_as_uint(
+        slab < 2 ? (slab == 0 ? p.w2.x : p.w2.y)
+                 : (slab < 4 ? (slab == 2 ? p.w2.z : p.w2.w) : (slab == 4 ? p.w3.x : p.w3.y)));
+    const int w2 = (int)(bx >> 20);
+    // an approximate reciprocal suffices: (rem + 1/2) / w2 lies at least 1/(2 w2)
+    // from an integer and rem < 256
+    const int dj = (int)(((float)rem + 0.5f) * __fdividef(1.0f, (float)w2));
+    const int j = (int)(bx & 1023u) + dj, l = (int)((bx >> 10) & 1023u) + rem - dj * w2;
+    x = m == 0 ? c : j;
+    y = m == 1 ? c : (m == 0 ? j : l);
+    z = m == 2 ? c : l;
+    return true;
+  }
   int j0, j1, l0, l1;
   slab_box(am, a1, a2, p.w0.w, p.w1.w, p.w2.x, p.w2.y, p.w2.z, p.w2.w, n, c, j0, j1, l0, l1);
   const int w2 = (bits & (1u << 29)) ? l1 - l0 + 1 : W2;
@@ -226,28 +260,16 @@ __device__ __forceinline__ void add_fragment(const GridDev& g, float3 a, float3 
             fragment_word(g, a, b, n0, n1, en0, en1, x, y, z, F, sq));
 }
 
+// A record slot pass 1 took for a candidate it did not keep.
+constexpr unsigned long long kNoRecord = ~0ull;
+
 __device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, uint32_t seg) {
-  const uint32_t r = atomicAdd(&g.st->rec_cnt, 1u);
+  const unsigned long long r = atomicAdd(&g.st->rec_cnt, 1ull);
   if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg;
   else set_err(g.st, kErrOverflow);
 }
 
-constexpr int kWarpRecords = 256;  // records a warp stages before one global append
-
-// Append a warp's staged records with one atomic (all lanes call).
-__device__ __forceinline__ void flush_records(const GridDev& g, const unsigned long long* srec, int n,
-                                              int lane) {
-  if (n == 0) return;
-  uint32_t r0 = 0;
-  if (lane == 0) r0 = atomicAdd(&g.st->rec_cnt, (uint32_t)n);
-  r0 = __shfl_sync(FULLW, r0, 0);
-  for (int k = lane; k < n; k += 32) {
-    const uint32_t r = r0 + (uint32_t)k;
-    if (r < g.rec_cap) g.rec[r] = srec[k];
-    else set_err(g.st, kErrOverflow);
-  }
-  __syncwarp();
-}
+constexpr int kWarpRecords = 256;  // pass 2: culled records a warp stages per append
 
 // Append a warp's staged culled records to cq (all lanes call); records past
 // the queue's capacity are counted but dropped, which sends the repair rounds
@@ -293,14 +315,12 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   }
   unsigned long long F = 0, sq = 0, ex = 0;
   const unsigned lt = (1u << lane) - 1u;
-  __shared__ unsigned long long s_rec[8][kWarpRecords];
   // every lane's walk, packed, read by the lanes that take its candidates
   __shared__ PackedWalk s_w[256];
   __shared__ float4 s_n[2][256];  // clip normals at v0 and v1
   __shared__ uint32_t s_seg[256];  // segment id of each lane's walk
-  unsigned long long* srec = s_rec[threadIdx.x >> 5];
   const int tid = threadIdx.x, wb = tid & ~31;
-  int wcount = 0;  // records staged by this warp (uniform)
+  uint32_t wcount = 0;  // records this warp has written (uniform)
   // segment id of lane j's walk
   auto seg_of = [&](int j) { return order ? s_seg[wb + j] : (uint32_t)(base + j); };
   // The warp's candidates, segment after segment, are numbered 0..total-1;
@@ -313,6 +333,25 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     if (lane >= o) incl += v;
   }
   const uint32_t total = __shfl_sync(FULLW, incl, 31);
+  // record slots: one atomic per block for all its candidates, warp shares in
+  // warp order (a fragment per warp step took 2-3 flushes of staged records
+  // per warp on one global counter, which contended)
+  __shared__ uint32_t s_wtot[8];
+  __shared__ unsigned long long s_rbase;
+  const int wid = threadIdx.x >> 5;
+  if (lane == 0) s_wtot[wid] = total;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t sum = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      const uint32_t t = s_wtot[k];
+      s_wtot[k] = sum;
+      sum += t;
+    }
+    s_rbase = sum ? atomicAdd(&g.st->rec_cnt, (unsigned long long)sum) : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long rbase = s_rbase + s_wtot[wid];
   if (w.n) {
     if (order) s_seg[tid] = (uint32_t)i;
     s_w[tid] = pack_walk(w, en, incl - w.n);
@@ -345,13 +384,12 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
         atomicAdd(&g.word[idx], inc);
       }
     }
-    if (keep) srec[wcount + __popc(am & lt)] = ((unsigned long long)idx << 32) | seg_of(j);
-    wcount += __popc(am);
-    if (wcount > kWarpRecords - 32) {
-      __syncwarp();
-      flush_records(g, srec, wcount, lane);
-      wcount = 0;
+    if (keep) {
+      const unsigned long long r = rbase + wcount + __popc(am & lt);
+      if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg_of(j);
+      else set_err(g.st, kErrOverflow);
     }
+    wcount += __popc(am);
   };
   // stage 2 for queued entries below cnt (all lanes call)
   auto stage2 = [&](uint32_t cnt) {
@@ -406,8 +444,10 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   }
   __syncwarp();
   stage2(un);
-  __syncwarp();
-  flush_records(g, srec, wcount, lane);
+  for (uint32_t k = wcount + lane; k < total; k += 32) {  // slots of candidates not kept
+    const unsigned long long r = rbase + k;
+    if (r < g.rec_cap) g.rec[r] = kNoRecord;
+  }
   flush_counters(g.st, F, sq, ex);
 }
 
@@ -449,7 +489,8 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
   unsigned long long* cq = reinterpret_cast<unsigned long long*>(g.xq);
   const bool compact = mode == 2 && g.st->cq_cnt <= g.xq_cap;
   const unsigned long long* src = compact ? cq : g.rec;
-  const uint32_t cnt = compact ? g.st->cq_cnt : min(g.st->rec_cnt, g.rec_cap);
+  const unsigned long long cnt =
+      compact ? g.st->cq_cnt : min(g.st->rec_cnt, (unsigned long long)g.rec_cap);
   const uint32_t* sel = mode == 2 ? need : g.vis;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -458,12 +499,13 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
   unsigned long long listed = 0;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t e0 = warp * 32; e0 < cnt; e0 += n_warps * 32) {
-    const uint32_t e = e0 + lane;
-    bool skip = true;
+  for (unsigned long long e0 = warp * 32ull; e0 < cnt; e0 += n_warps * 32ull) {
+    const unsigned long long e = e0 + lane;
+    bool skip = true, have = false;
     unsigned long long r = 0;
-    if (e < cnt) {
-      r = __ldcs(&src[e]);
+    if (e < cnt) r = __ldcs(&src[e]);
+    if (e < cnt && r != kNoRecord) {
+      have = true;
       const uint32_t idx = (uint32_t)(r >> 32);
       skip = mode != 0 && !bit_set(sel, idx);
       if (!skip) {
@@ -477,7 +519,7 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
       }
     }
     if (mode == 1) {
-      const bool keep = e < cnt && skip;
+      const bool keep = have && skip;
       const unsigned km = __ballot_sync(FULLW, keep);
       if (keep) srec[wcount + __popc(km & lt)] = r;
       wcount += __popc(km);

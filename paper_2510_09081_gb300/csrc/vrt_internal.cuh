@@ -41,8 +41,7 @@ struct DevStatus {
   unsigned long long F;              // fragments of pass 1
   unsigned long long sum_q;          // occupancy codes of pass 1
   unsigned long long exact_decisions;  // list decisions on the exact path
-  unsigned int rec_cnt;              // fragment records appended by pass 1
-  unsigned int rec_pad;
+  unsigned long long rec_cnt;        // record slots taken by pass 1 and its exact path
   // --- reset by every list build from here on
   unsigned long long sum_count_field;  // checked by the scan
   unsigned long long sum_occ_field;
