@@ -217,10 +217,45 @@ __device__ __forceinline__ bool decode_candidate(const PackedWalk& p, int n, uin
   return true;
 }
 
-__device__ __forceinline__ void queue_exact(const GridDev& g, uint32_t seg, int x, int y, int z) {
-  const uint32_t q = atomicAdd(&g.st->xq_cnt, 1u);
-  if (q < g.xq_cap) g.xq[q] = make_uint2(seg, pack_voxel(x, y, z));
-  else set_err(g.st, kErrOverflow);
+// Queue the (segment, voxel) pairs of the lanes with q set for the exact
+// decision, one atomic per warp (all lanes call).
+__device__ __forceinline__ void queue_exact(const GridDev& g, bool q, uint32_t seg, int x, int y,
+                                            int z, int lane) {
+  const unsigned m = __ballot_sync(FULLW, q);
+  if (!m) return;
+  uint32_t base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(&g.st->xq_cnt, (uint32_t)__popc(m));
+  base = __shfl_sync(FULLW, base, __ffs(m) - 1);
+  if (q) {
+    const uint32_t k = base + __popc(m & ((1u << lane) - 1u));
+    if (k < g.xq_cap) g.xq[k] = make_uint2(seg, pack_voxel(x, y, z));
+    else set_err(g.st, kErrOverflow);
+  }
+}
+
+// The block's pass-1 counters into the status, three atomics per block (all
+// threads of the block call).
+__device__ __forceinline__ void flush_counters_block(DevStatus* st, unsigned long long F,
+                                                     unsigned long long q, unsigned long long ex) {
+  __shared__ unsigned long long s_c[3][8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    F += __shfl_down_sync(FULLW, F, o);
+    q += __shfl_down_sync(FULLW, q, o);
+    ex += __shfl_down_sync(FULLW, ex, o);
+  }
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_c[0][wid] = F;
+    s_c[1][wid] = q;
+    s_c[2][wid] = ex;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    unsigned long long v = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += s_c[threadIdx.x][k];
+    if (v) atomicAdd(threadIdx.x == 0 ? &st->F : (threadIdx.x == 1 ? &st->sum_q : &st->exact_decisions), v);
+  }
 }
 
 __device__ __forceinline__ void flush_counters(DevStatus* st, unsigned long long F,
@@ -400,12 +435,10 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
       j = (int)it.x;
       unpack_voxel(it.y, x, y, z);
       p = s_w[wb + j];
-      dec = seg_stage2_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
-      if (dec < 0) {
-        queue_exact(g, seg_of(j), x, y, z);
-        ++ex;
-      }
+      dec = g.force_exact ? -1 : seg_stage2_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
+      if (dec < 0) ++ex;
     }
+    queue_exact(g, dec < 0, (uint32_t)lane < cnt ? seg_of(j) : 0u, x, y, z, lane);
     emit(dec > 0, j, p, x, y, z);
   };
   for (uint32_t t0 = 0; t0 < total; t0 += 32) {
@@ -419,14 +452,9 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     PackedWalk p;
     if (gq < total) {
       p = s_w[wb + j];
-      if (decode_candidate(p, g.n, gq - __float_as_uint(p.w3.w), x, y, z)) {
-        if (g.force_exact) {
-          queue_exact(g, seg_of(j), x, y, z);
-          ++ex;
-        } else {
-          dec = seg_stage1_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
-        }
-      }
+      // with the force_exact test option every pair goes on to the exact path
+      if (decode_candidate(p, g.n, gq - __float_as_uint(p.w3.w), x, y, z))
+        dec = g.force_exact ? -1 : seg_stage1_at(f3(p.w0), f3(p.w1), x, y, z, g.rl);
     }
     const unsigned um = __ballot_sync(FULLW, dec < 0);
     if (dec < 0) uq[un + __popc(um & lt)] = make_uint2((uint32_t)j, pack_voxel(x, y, z));
@@ -448,7 +476,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
     const unsigned long long r = rbase + k;
     if (r < g.rec_cap) g.rec[r] = kNoRecord;
   }
-  flush_counters(g.st, F, sq, ex);
+  flush_counters_block(g.st, F, sq, ex);
 }
 
 // Exact decisions of pass 1's undecided pairs.
