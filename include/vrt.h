@@ -275,7 +275,7 @@ vrt_status vrt_read_shading(vrt_grid g, float* values_host, uint8_t* valid_host)
  * up to this length share the warp entry by entry in the trace; longer ones
  * take the whole-warp path (one list at a time). The image does not depend on
  * it; for testing that path.
- * VRT_OPT_TRACE_RAY_KEYS (9): value in [1, 40] (default 40): hit slots per
+ * VRT_OPT_TRACE_RAY_KEYS (9): value in [1, 32] (default 32): hit slots per
  * transparent ray and voxel on the shared-entry path; a ray with more hits in
  * one voxel takes the whole-warp path for it. The image does not depend on
  * it; for testing.

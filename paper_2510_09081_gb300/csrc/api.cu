@@ -1232,7 +1232,7 @@ vrt_status vrt_set_option(vrt_grid g, int32_t option, int64_t value) {
     return VRT_OK;
   }
   if (option == VRT_OPT_TRACE_RAY_KEYS) {
-    if (value < 1 || value > kRayKeys) return fail(g, VRT_ERR_INVALID_ARG, "ray key slots must be in [1, 40]");
+    if (value < 1 || value > kRayKeys) return fail(g, VRT_ERR_INVALID_ARG, "ray key slots must be in [1, 32]");
     g->ray_keys = (uint32_t)value;
     return VRT_OK;
   }

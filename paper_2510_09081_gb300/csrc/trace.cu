@@ -53,7 +53,10 @@ namespace vrt {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kLaneKeys = 4;              // transparent, shared list: keys kept per lane per scan
 // kRayKeys (vrt_internal.cuh): hit slots per transparent ray on the shared-entry
-// path, 40 KB of shared memory per block; A.ray_keys <= kRayKeys of them are used
+// path, 32 KB of shared memory per block; A.ray_keys <= kRayKeys of them are used.
+// 40 slots (40 KB) left the 4 resident blocks of an SM so little L1 that the
+// trace of a sparse 512^3 set at 4K ran 5% slower; 24 slots sent too many rays
+// to the whole-warp path (bundles trace 2.5% slower).
 constexpr int kTraceThreads = 128;
 constexpr int kStepRound = 1;             // tile trace: DDA steps a walking lane takes per round
 

@@ -21,7 +21,7 @@ constexpr float kTStop = 1e-4f;                // transmittance where a ray stop
 constexpr int kMaxRepairRounds = 4;
 constexpr uint32_t kRayQueueLimit = 8;          // culled voxels one ray queues per round
 constexpr uint32_t kShortList = 1024;           // trace: longer lists go to the whole-warp path
-constexpr int kRayKeys = 40;                    // trace: hit slots per transparent ray on the shared-entry path
+constexpr int kRayKeys = 32;                    // trace: hit slots per transparent ray on the shared-entry path
 constexpr int kBrickDistMax = 15;               // cap of the empty-brick distance field
 constexpr int kMipsF32 = 0, kMipsF16 = 1, kMipsBF16 = 2;  // occupancy pyramid storage
 

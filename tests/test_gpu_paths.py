@@ -74,7 +74,7 @@ def test_few_ray_key_slots_match_oracle():
     vrt.set_option(r.h, vrt.OPT_TRACE_RAY_KEYS, 2)
     few = _image(r, cam, 0.3)
     with pytest.raises(vrt.VrtError):
-        vrt.set_option(r.h, vrt.OPT_TRACE_RAY_KEYS, 41)
+        vrt.set_option(r.h, vrt.OPT_TRACE_RAY_KEYS, 33)
     r.close()
     _assert_parity(compare_image(*few, ref))
     for a, b in zip(default, few):
