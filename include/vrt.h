@@ -67,7 +67,7 @@ typedef struct {
                              0.9 (L + 2 rl + 2)(2 rl + 2)^2, at least 16,
                              entries per uploaded vertex, with L the mean
                              segment length of the vrt_upload_segments call
-                             and rl = radius + 2^-9; at most 2^32 - 1;
+                             and rl = radius + 2^-9; at most 3 * 2^30 - 1;
                              exceeding it reports VRT_ERR_OVERFLOW */
 } vrt_grid_desc;
 

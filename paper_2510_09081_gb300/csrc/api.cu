@@ -566,7 +566,7 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
   const double per = std::max(16.0, 0.9 * (mean_len + 2 * rl + 2) * (2 * rl + 2) * (2 * rl + 2));
   unsigned long long cap = g->max_frag_desc ? g->max_frag_desc
                                             : (unsigned long long)(per * (double)std::max(V, 1ll));
-  cap = std::min<unsigned long long>(cap, 0xffffffffull);
+  cap = std::min<unsigned long long>(cap, kCulledStart - 1ull);
   if (cap != g->list_cap || !g->lists) {
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
     dfree(g, g->lists);

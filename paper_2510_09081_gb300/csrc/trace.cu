@@ -223,11 +223,11 @@ __device__ int advance(const TraceArgs& A, Ray& R, int budget) {
                           ((uint32_t)(R.vy >> 2) << A.g.log2nb) | (uint32_t)(R.vx >> 2);
     const uint32_t idx = brick_index(R.vx, R.vy, R.vz, A.g.log2nb);
     // the step's loads are independent: issue them together (one latency, not
-    // up to four in sequence); the word, mark and list end go unused in an
+    // up to three in sequence); the word and the list end -- at or above
+    // kCulledStart when the cull gave the voxel no list -- go unused in an
     // empty brick
     const int kd = __ldg(&A.g.bdist[bidx]);
     const uint32_t wv = __ldg(&A.g.word[idx]);
-    const uint32_t vb = __ldg(&A.g.vis[idx >> 5]);
     const uint32_t cv = __ldg(&A.g.cur[idx]);
     if (kd > 0) {
       // cross the cube of empty bricks within kd - 1 of this one: low corner
@@ -276,7 +276,7 @@ __device__ int advance(const TraceArgs& A, Ray& R, int budget) {
       inside = R.vz >= 0 && R.vz < n;
     }
     if (cnt) {
-      if (!((vb >> (idx & 31)) & 1u)) {
+      if (cv >= kCulledStart) {  // the cull gave it no list
         // culled voxel on the ray: queue it, march on as if it were empty; at
         // the first one, keep the ray's state for the re-trace to resume from
         if (R.n_queued == 0 && A.resume) {

@@ -535,6 +535,9 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
     if (e < cnt && r != kNoRecord) {
       have = true;
       const uint32_t idx = (uint32_t)(r >> 32);
+      // (taking the slot first and reading the cull's verdict from the
+      // kCulledStart cursor saves the mark's load on listed records but adds a
+      // contended atomic per culled one: ABC pass 2 1.17 -> 3.54 ms)
       skip = mode != 0 && !bit_set(sel, idx);
       if (!skip) {
         const uint32_t slot = atomicAdd(&g.cur[idx], 1u);

@@ -35,6 +35,10 @@ constexpr uint32_t kErrTimeout = 4u;    // bounded wait gave up
 constexpr uint32_t kErrBounds = 8u;     // index out of its buffer
 constexpr uint32_t kErrRepair = 16u;    // repair rounds exhausted
 
+// List start the scan gives a voxel the cull left without a list; list
+// capacities stay below it, so a cursor at or above it marks such a voxel.
+constexpr uint32_t kCulledStart = 0xC0000000u;
+
 struct DevStatus {
   unsigned int err;
   unsigned int occupied_voxels;
@@ -102,7 +106,7 @@ struct GridDev {
   float occ_scale;
   int force_exact;
   uint32_t* word;          // [n^3] packed (occupancy code sum << 16) | count
-  uint32_t* cur;           // [n^3] list end cursor (start = cur - count)
+  uint32_t* cur;           // [n^3] list end cursor (start = cur - count); >= kCulledStart: no list
   uint32_t* vis;           // [n^3 / 32] voxel has a list
   const uint8_t* bdist;    // [bricks] Chebyshev distance (bricks) to an occupied brick, capped
   uint32_t* lists;         // [list_cap]
