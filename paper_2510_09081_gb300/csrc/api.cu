@@ -45,6 +45,7 @@ struct vrt_grid_s {
   uint2* xq = nullptr;      // pairs the fp32 filter left to the exact path
   uint32_t xq_cap = 0;
   unsigned long long* rec = nullptr;  // fragment records of pass 1 (list_cap entries)
+  uint16_t* rank = nullptr;           // each record's rank within its voxel (list_cap entries)
   unsigned long long* tile_state = nullptr;
   uint32_t n_tiles = 0;
   void* mips = nullptr;            // occupancy pyramid (room for fp32 texels)
@@ -164,7 +165,7 @@ GridDev gdev(vrt_grid g) {
   d.word = g->word; d.cur = g->cur; d.vis = g->vis; d.bdist = g->bdist;
   d.lists = g->lists; d.list_cap = g->list_cap;
   d.xq = g->xq; d.xq_cap = g->xq_cap;
-  d.rec = g->rec; d.rec_cap = (uint32_t)g->list_cap;
+  d.rec = g->rec; d.rank = g->rank; d.rec_cap = (uint32_t)g->list_cap;
   d.st = g->st;
   return d;
 }
@@ -430,7 +431,7 @@ void free_all(vrt_grid g) {
   dfree(g, g->raw); dfree(g, g->flags); dfree(g, g->pos); dfree(g, g->nrm); dfree(g, g->order);
   dfree(g, g->word); dfree(g, g->cur); dfree(g, g->vis); dfree(g, g->bdist); dfree(g, g->btmp);
   dfree(g, g->need); dfree(g, g->eroded); dfree(g, g->cdist); dfree(g, g->emean); dfree(g, g->lists); dfree(g, g->tile_state);
-  dfree(g, g->xq); dfree(g, g->rec);
+  dfree(g, g->xq); dfree(g, g->rec); dfree(g, g->rank);
   dfree(g, g->mips); dfree(g, g->vq[0]); dfree(g, g->vq[1]); dfree(g, g->pq[0]); dfree(g, g->pq[1]);
   dfree(g, g->resume);
   dfree(g, g->shade); dfree(g, g->shade_mask);
@@ -571,9 +572,11 @@ vrt_status vrt_upload_segments(vrt_grid g, const float* xyz, int32_t stride, int
     VRT_CUDA(g, cudaStreamSynchronize(g->stream));
     dfree(g, g->lists);
     dfree(g, g->rec);
+    dfree(g, g->rank);
     g->list_cap = 0;
     VRT_CUDA(g, dalloc(g, &g->lists, (size_t)cap));
     VRT_CUDA(g, dalloc(g, &g->rec, (size_t)cap));
+    VRT_CUDA(g, dalloc(g, &g->rank, (size_t)cap));
     g->list_cap = cap;
   }
   {

@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(GridDev g, int all_visibl
   uint32_t outv[kScanItems];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    outv[k] = ((visw >> k) & 1u) ? run : kCulledStart;
     run += val[k];
+    outv[k] = ((visw >> k) & 1u) ? run : kCulledStart;  // list end (pass 2 fills below it)
   }
   uint4* dst = reinterpret_cast<uint4*>(g.cur + base);
 #pragma unroll

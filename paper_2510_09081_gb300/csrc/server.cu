@@ -138,9 +138,9 @@ uint64_t estimate_bytes(const ServerSet& st) {
   const double per = std::max(16.0, 0.9 * (mean_len + 2 * rl + 2) * (2 * rl + 2) * (2 * rl + 2));
   const uint64_t cap = st.desc.max_fragments ? st.desc.max_fragments : (uint64_t)(per * V);
   const uint64_t xq = std::max<uint64_t>(4 * V, 1ull << 22);
-  // words, cursors, marks, fields, pyramid; vertices; lists and records; exact
-  // queue; cull scratch; voxel-space shading field and mask; pixel queues at 1080p
-  return nv * 17 + nv / 4 + V * 45 + cap * 12 + xq * 8 + nv * 5 + nv * 4 + nv / 8 + 2073600ull * 40;
+  // words, cursors, marks, fields, pyramid; vertices; lists, records and ranks;
+  // exact queue; cull scratch; voxel-space shading field and mask; pixel queues at 1080p
+  return nv * 17 + nv / 4 + V * 45 + cap * 14 + xq * 8 + nv * 5 + nv * 4 + nv / 8 + 2073600ull * 40;
 }
 
 void CUDART_CB on_frame_done(void* arg) {

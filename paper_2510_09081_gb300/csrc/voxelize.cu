@@ -23,12 +23,14 @@
 // 32-bit atomic (Sec. 3.1) -- on grids of side 512 and more one per distinct
 // voxel of a warp step, the increments of lanes that share the voxel summed
 // first -- and writes the fragment as an 8-byte record (voxel << 32 |
-// segment). A block takes record slots for all its walks' candidates with one
-// atomic; each warp writes its fragments at the start of its share and marks
-// the rest (candidates that were not kept) kNoRecord. The paper re-voxelizes in its
-// second pass to save memory; with the records in HBM the second pass is a
-// streaming scatter instead: for every record whose voxel received a list,
-// bump the voxel's cursor and write the segment id (Sec. 3.3).
+// segment) with its rank, the count field the atomic returned (fragments of
+// the voxel added before it), beside it. A block takes record slots for all its
+// walks' candidates with one atomic; each warp writes its fragments at the
+// start of its share and marks the rest (candidates that were not kept)
+// kNoRecord. The paper re-voxelizes in its second pass to save memory; with the
+// records in HBM the second pass is a streaming scatter instead: for every
+// record whose voxel received a list, write the segment id at the slot its
+// rank gives below the voxel's list end (Sec. 3.3), with no atomic.
 #include "launch.h"
 
 namespace vrt {
@@ -288,20 +290,27 @@ __device__ __forceinline__ uint32_t fragment_word(const GridDev& g, float3 a, fl
   return (q << 16) | 1u;
 }
 
-__device__ __forceinline__ void add_fragment(const GridDev& g, float3 a, float3 b, float3 n0,
-                                             float3 n1, bool en0, bool en1, int x, int y, int z,
-                                             unsigned long long& F, unsigned long long& sq) {
-  atomicAdd(&g.word[brick_index(x, y, z, g.log2nb)],
-            fragment_word(g, a, b, n0, n1, en0, en1, x, y, z, F, sq));
+// Adds a fragment to its voxel's packed word; returns its rank in the voxel.
+__device__ __forceinline__ uint32_t add_fragment(const GridDev& g, float3 a, float3 b, float3 n0,
+                                                 float3 n1, bool en0, bool en1, int x, int y,
+                                                 int z, unsigned long long& F,
+                                                 unsigned long long& sq) {
+  return atomicAdd(&g.word[brick_index(x, y, z, g.log2nb)],
+                   fragment_word(g, a, b, n0, n1, en0, en1, x, y, z, F, sq)) & 0xffffu;
 }
 
 // A record slot pass 1 took for a candidate it did not keep.
 constexpr unsigned long long kNoRecord = ~0ull;
 
-__device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, uint32_t seg) {
+__device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, uint32_t seg,
+                                              uint32_t rank) {
   const unsigned long long r = atomicAdd(&g.st->rec_cnt, 1ull);
-  if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg;
-  else set_err(g.st, kErrOverflow);
+  if (r < g.rec_cap) {
+    g.rec[r] = ((unsigned long long)idx << 32) | seg;
+    g.rank[r] = (uint16_t)rank;
+  } else {
+    set_err(g.st, kErrOverflow);
+  }
 }
 
 constexpr int kWarpRecords = 256;  // pass 2: culled records a warp stages per append
@@ -400,9 +409,22 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   __shared__ uint2 s_uq[8][64];  // (owner lane, packed voxel)
   uint2* uq = s_uq[threadIdx.x >> 5];
   uint32_t un = 0;  // queued (uniform)
-  // a kept fragment: occupancy into the packed word, record staged (all lanes call)
+  // A fragment's rank is stored one emit later, so the latency of the
+  // returning atomic that gives it overlaps a step of work: pend_r is the
+  // record slot still waiting for its rank, the rank being pend_off plus the
+  // word that lane pend_src's atomic returned (its own, without merging).
+  unsigned long long pend_r = ~0ull;
+  uint32_t pend_old = 0, pend_off = 0;
+  int pend_src = lane;
+  auto flush_rank = [&]() {  // all lanes call
+    const uint32_t old = AGG ? __shfl_sync(FULLW, pend_old, pend_src) : pend_old;
+    if (pend_r < g.rec_cap) g.rank[pend_r] = (uint16_t)(old + pend_off);  // low 16 bits: count
+    pend_r = ~0ull;
+  };
+  // a kept fragment: occupancy into the packed word, record written (all lanes call)
   auto emit = [&](bool keep, int j, const PackedWalk& p, int x, int y, int z) {
     uint32_t idx = 0;
+    flush_rank();
     const unsigned am = __ballot_sync(FULLW, keep);
     if (keep) {
       idx = brick_index(x, y, z, g.log2nb);
@@ -412,17 +434,24 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
       if (AGG) {
         // lanes adding to the same voxel (neighbouring segments of the warp
         // share voxels) sum their increments: one atomic per voxel and step
+        // and rank after the leader's count, in lane order
         const unsigned peers = __match_any_sync(am, idx);
         const uint32_t sum = __reduce_add_sync(peers, inc);
-        if (lane == __ffs(peers) - 1) atomicAdd(&g.word[idx], sum);
+        pend_src = __ffs(peers) - 1;
+        pend_off = __popc(peers & lt);
+        if (lane == pend_src) pend_old = atomicAdd(&g.word[idx], sum);
       } else {
-        atomicAdd(&g.word[idx], inc);
+        pend_old = atomicAdd(&g.word[idx], inc);
       }
     }
     if (keep) {
       const unsigned long long r = rbase + wcount + __popc(am & lt);
-      if (r < g.rec_cap) g.rec[r] = ((unsigned long long)idx << 32) | seg_of(j);
-      else set_err(g.st, kErrOverflow);
+      if (r < g.rec_cap) {
+        g.rec[r] = ((unsigned long long)idx << 32) | seg_of(j);
+        pend_r = r;
+      } else {
+        set_err(g.st, kErrOverflow);
+      }
     }
     wcount += __popc(am);
   };
@@ -472,6 +501,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   }
   __syncwarp();
   stage2(un);
+  flush_rank();
   for (uint32_t k = wcount + lane; k < total; k += 32) {  // slots of candidates not kept
     const unsigned long long r = rbase + k;
     if (r < g.rec_cap) g.rec[r] = kNoRecord;
@@ -490,9 +520,10 @@ __global__ void __launch_bounds__(256) k_exact1(const float4* __restrict__ pos,
     unpack_voxel(it.y, x, y, z);
     const float4 p0 = pos[it.x], p1 = pos[it.x + 1];
     if (!seg_exact_at(f3(p0), f3(p1), x, y, z, g.RL)) continue;
-    add_fragment(g, f3(p0), f3(p1), f3(nrm[it.x]), f3(nrm[it.x + 1]),
-                 __float_as_uint(p0.w) & kClipOn, __float_as_uint(p1.w) & kClipOn, x, y, z, F, sq);
-    append_record(g, brick_index(x, y, z, g.log2nb), it.x);
+    const uint32_t rank =
+        add_fragment(g, f3(p0), f3(p1), f3(nrm[it.x]), f3(nrm[it.x + 1]),
+                     __float_as_uint(p0.w) & kClipOn, __float_as_uint(p1.w) & kClipOn, x, y, z, F, sq);
+    append_record(g, brick_index(x, y, z, g.log2nb), it.x, rank);
   }
   unsigned long long z0 = 0;
   flush_counters(g.st, F, sq, z0);
@@ -504,12 +535,14 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t i) {
 
 // Pass 2: stream the fragment records; mode 0 lists every fragment, mode 1
 // those whose voxel the cull marked, mode 2 (repair) those whose voxel's
-// `need` bit is set. (One returning cursor atomic per listed record: merging
-// the lanes of a warp that list into the same voxel first, by a match on the
-// voxel index, measured slower -- the match costs more than the atomics it
-// saves.) Mode 1 also copies the records of unmarked voxels to the
-// (by then unused) exact-path queue, warp-staged, so that the repair rounds
-// stream only those; when they do not all fit, the repair streams every record.
+// `need` bit is set. Modes 0 and 1 read the voxel's list end from the scan's
+// cursor -- kCulledStart when the cull gave it no list -- and write the segment
+// id at end - 1 - rank: no atomic, and the cursor is the cull's verdict, so the
+// mark is not read. The repair, whose copied records carry no rank, bumps the
+// cursor of each listed voxel from its list start with a returning atomic.
+// Mode 1 also copies the records of unmarked voxels to the (by then unused)
+// exact-path queue, warp-staged, so that the repair rounds stream only those;
+// when they do not all fit, the repair streams every record.
 __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint32_t* __restrict__ need,
                                                  const uint32_t* __restrict__ pending) {
   if (mode == 2 && *pending == 0) return;
@@ -519,7 +552,6 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
   const unsigned long long* src = compact ? cq : g.rec;
   const unsigned long long cnt =
       compact ? g.st->cq_cnt : min(g.st->rec_cnt, (unsigned long long)g.rec_cap);
-  const uint32_t* sel = mode == 2 ? need : g.vis;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long* srec = s_rec[threadIdx.x >> 5];
@@ -531,16 +563,24 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
     const unsigned long long e = e0 + lane;
     bool skip = true, have = false;
     unsigned long long r = 0;
-    if (e < cnt) r = __ldcs(&src[e]);
+    uint32_t rank = 0;
+    if (e < cnt) {
+      r = __ldcs(&src[e]);
+      if (mode != 2) rank = __ldcs(&g.rank[e]);
+    }
     if (e < cnt && r != kNoRecord) {
       have = true;
       const uint32_t idx = (uint32_t)(r >> 32);
-      // (taking the slot first and reading the cull's verdict from the
-      // kCulledStart cursor saves the mark's load on listed records but adds a
-      // contended atomic per culled one: ABC pass 2 1.17 -> 3.54 ms)
-      skip = mode != 0 && !bit_set(sel, idx);
+      uint32_t slot = 0;
+      if (mode != 2) {
+        const uint32_t end = __ldg(&g.cur[idx]);
+        skip = end >= kCulledStart;
+        slot = end - 1u - rank;
+      } else {
+        skip = !bit_set(need, idx);
+        if (!skip) slot = atomicAdd(&g.cur[idx], 1u);
+      }
       if (!skip) {
-        const uint32_t slot = atomicAdd(&g.cur[idx], 1u);
         if (slot < g.list_cap) {
           g.lists[slot] = (uint32_t)r;
           ++listed;

@@ -114,6 +114,7 @@ struct GridDev {
   uint2* xq;               // [xq_cap] undecided (segment id, packed voxel) pairs
   uint32_t xq_cap;
   unsigned long long* rec; // [rec_cap] fragment records: voxel << 32 | segment
+  uint16_t* rank;          // [rec_cap] a record's position among its voxel's fragments
   uint32_t rec_cap;
   DevStatus* st;
 };
