@@ -696,8 +696,11 @@ vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* 
     if (!g->eroded) VRT_CUDA(g, dalloc(g, &g->eroded, nv));
     if (!g->cdist) VRT_CUDA(g, dalloc(g, &g->cdist, nv / 64));
     if (!g->emean) VRT_CUDA(g, dalloc(g, &g->emean, nv / 64));
+    // the exact-path queue is free between pass 1's exact decisions and pass 2:
+    // the cull keeps its queue of occupied voxels there
     g->launches += launch_cull(d, host_cam(cam), p->alpha, g->eroded, g->btmp, g->cdist, g->emean,
-                               g->cull_depth, g->stream);
+                               g->cull_depth, reinterpret_cast<uint32_t*>(g->xq),
+                               2ull * g->xq_cap, g->stream);
   } else {
     VRT_CUDA(g, cudaMemsetAsync(g->vis, 0xff, nv / 8, g->stream));
   }

@@ -34,41 +34,87 @@ __device__ __forceinline__ uint32_t occ8(const GridDev& g, int x, int y, int z) 
 }
 
 // Erosion, and per brick whether any voxel keeps eroded occupancy (0) or none
-// does (kBrickDistMax), the seed of the march's skipping field. A block covers
-// 4 bricks of 64 consecutive voxels.
+// does (kBrickDistMax), the seed of the march's skipping field, and the mean
+// eroded occupancy. A thread takes one x-row of a brick (four consecutive
+// words, one 16-byte load), so 16 threads cover a brick and a warp two; the
+// rows next to it in y and z are four consecutive words too. The thread also
+// clears its row's bits of the cull marks, and queues the row's voxels that
+// hold segments for the march (one atomic per warp) when occq is given.
+__device__ __forceinline__ uint32_t occ8w(const GridDev& g, uint32_t w) {
+  return min(255u, (uint32_t)((float)(w >> 16) * (255.0f / g.occ_scale)));
+}
+
+__device__ __forceinline__ uint4 row_words(const GridDev& g, int x, int y, int z) {
+  if ((unsigned)y >= (unsigned)g.n || (unsigned)z >= (unsigned)g.n) return make_uint4(0u, 0u, 0u, 0u);
+  return __ldg(reinterpret_cast<const uint4*>(g.word) + (brick_index(x, y, z, g.log2nb) >> 2));
+}
+
 __global__ void __launch_bounds__(256) k_erode(GridDev g, uint8_t* __restrict__ eroded,
                                                uint8_t* __restrict__ ebrick,
-                                               float* __restrict__ emean) {
-  __shared__ uint32_t s_any[4], s_sum[4];
-  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (threadIdx.x < 4) s_any[threadIdx.x] = s_sum[threadIdx.x] = 0;
-  __syncthreads();
-  uint32_t e = 0;
-  if (idx < (uint32_t)g.n * g.n * g.n) {
-    int x, y, z;
-    brick_coords(idx, g.log2nb, x, y, z);
-    e = occ8(g, x, y, z);
-    if (e) {
-      e = min(e, occ8(g, x - 1, y, z));
-      e = min(e, occ8(g, x + 1, y, z));
-      e = min(e, occ8(g, x, y - 1, z));
-      e = min(e, occ8(g, x, y + 1, z));
-      e = min(e, occ8(g, x, y, z - 1));
-      e = min(e, occ8(g, x, y, z + 1));
-    }
-    eroded[idx] = (uint8_t)e;
-  }
-  uint32_t esum = e;
+                                               float* __restrict__ emean,
+                                               uint32_t* __restrict__ occq,
+                                               unsigned long long occq_cap) {
+  const uint32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nrow = ((uint32_t)g.n * g.n * g.n) >> 2;  // a multiple of 32 (n >= 16)
+  const int lane = threadIdx.x & 31;
+  if (row >= nrow) return;  // whole warps
+  const uint32_t idx0 = row << 2;
+  int x, y, z;
+  brick_coords(idx0, g.log2nb, x, y, z);  // x: a multiple of 4
+  const uint4 w = __ldg(reinterpret_cast<const uint4*>(g.word) + row);
+  const uint32_t o[4] = {occ8w(g, w.x), occ8w(g, w.y), occ8w(g, w.z), occ8w(g, w.w)};
+  uint32_t e[4] = {o[0], o[1], o[2], o[3]};
+  if (o[0] | o[1] | o[2] | o[3]) {
+    // x neighbours: the row's own voxels, and one word of each neighbouring brick
+    const uint32_t xm = x > 0 ? occ8w(g, __ldg(&g.word[brick_index(x - 1, y, z, g.log2nb)])) : 0u;
+    const uint32_t xp = x + 4 < g.n ? occ8w(g, __ldg(&g.word[brick_index(x + 4, y, z, g.log2nb)])) : 0u;
+    const uint4 ym = row_words(g, x, y - 1, z), yp = row_words(g, x, y + 1, z);
+    const uint4 zm = row_words(g, x, y, z - 1), zp = row_words(g, x, y, z + 1);
+    const uint32_t wy0[4] = {ym.x, ym.y, ym.z, ym.w}, wy1[4] = {yp.x, yp.y, yp.z, yp.w};
+    const uint32_t wz0[4] = {zm.x, zm.y, zm.z, zm.w}, wz1[4] = {zp.x, zp.y, zp.z, zp.w};
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
-  if ((threadIdx.x & 31) == 0 && esum) {
-    atomicOr(&s_any[threadIdx.x >> 6], 1u);
-    atomicAdd(&s_sum[threadIdx.x >> 6], esum);
+    for (int k = 0; k < 4; ++k) {
+      if (!e[k]) continue;
+      uint32_t v = min(e[k], k > 0 ? o[k - 1] : xm);
+      v = min(v, k < 3 ? o[k + 1] : xp);
+      v = min(v, min(occ8w(g, wy0[k]), occ8w(g, wy1[k])));
+      v = min(v, min(occ8w(g, wz0[k]), occ8w(g, wz1[k])));
+      e[k] = v;
+    }
   }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    ebrick[blockIdx.x * 4 + threadIdx.x] = s_any[threadIdx.x] ? 0 : (uint8_t)kBrickDistMax;
-    emean[blockIdx.x * 4 + threadIdx.x] = (float)s_sum[threadIdx.x] * (1.0f / (255.0f * 64.0f));
+  reinterpret_cast<uchar4*>(eroded)[row] =
+      make_uchar4((uint8_t)e[0], (uint8_t)e[1], (uint8_t)e[2], (uint8_t)e[3]);
+  if ((row & 7u) == 0) g.vis[idx0 >> 5] = 0u;  // marks: set by the march
+  // the brick's 16 rows are lanes 0-15 or 16-31
+  uint32_t esum = e[0] + e[1] + e[2] + e[3];
+#pragma unroll
+  for (int off = 8; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
+  if ((lane & 15) == 0) {
+    const uint32_t b = row >> 4;
+    ebrick[b] = esum ? 0 : (uint8_t)kBrickDistMax;
+    emean[b] = (float)esum * (1.0f / (255.0f * 64.0f));
+  }
+  if (occq) {
+    const uint32_t om = ((w.x & 0xffffu) ? 1u : 0u) | ((w.y & 0xffffu) ? 2u : 0u) |
+                        ((w.z & 0xffffu) ? 4u : 0u) | ((w.w & 0xffffu) ? 8u : 0u);
+    const uint32_t nq = __popc(om);
+    uint32_t incl = nq;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t base = 0;
+    if (lane == 0 && total) base = atomicAdd(&g.st->occq_cnt, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    unsigned long long k = (unsigned long long)base + (incl - nq);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((om >> j) & 1u) {
+        if (k < occq_cap) occq[k] = idx0 + (uint32_t)j;
+        ++k;
+      }
   }
 }
 
@@ -84,14 +130,13 @@ struct CullCam {
 // Voxel steps of the march before it continues brick by brick.
 constexpr float kCullNear = 6.0f;
 
-__global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
-                                                 const uint8_t* __restrict__ eroded,
-                                                 const uint8_t* __restrict__ cdist,
-                                                 const float* __restrict__ emean) {
-  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
+// Whether occupied voxel idx keeps its list: inside the view frustum, and the
+// estimated optical depth between it and the camera stays below cc.depth_max.
+__device__ bool voxel_visible(const GridDev& g, const CullCam& cc, const uint8_t* __restrict__ eroded,
+                              const uint8_t* __restrict__ cdist, const float* __restrict__ emean,
+                              uint32_t idx) {
   bool visible = false;
-  if (idx < nvox && (__ldg(&g.word[idx]) & 0xffffu)) {
+  {
     int x, y, z;
     brick_coords(idx, g.log2nb, x, y, z);
     const float3 c = make_float3(x + 0.5f, y + 0.5f, z + 0.5f);
@@ -191,8 +236,37 @@ __global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
       }
     }
   }
+  return visible;
+}
+
+// One thread per voxel; the warp writes its 32 marks.
+__global__ void __launch_bounds__(256) k_visible(GridDev g, CullCam cc,
+                                                 const uint8_t* __restrict__ eroded,
+                                                 const uint8_t* __restrict__ cdist,
+                                                 const float* __restrict__ emean) {
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
+  const bool visible = idx < nvox && (__ldg(&g.word[idx]) & 0xffffu) &&
+                       voxel_visible(g, cc, eroded, cdist, emean, idx);
   const uint32_t m = __ballot_sync(0xffffffffu, visible);
   if ((threadIdx.x & 31) == 0 && idx < nvox) g.vis[idx >> 5] = m;
+}
+
+// One thread per queued occupied voxel (the erosion cleared the marks): every
+// lane of a warp marches, where one thread per voxel leaves the lanes of empty
+// voxels idle (ABC pathlines at 512^3 occupy a third of the grid).
+__global__ void __launch_bounds__(256) k_visible_queued(GridDev g, CullCam cc,
+                                                        const uint8_t* __restrict__ eroded,
+                                                        const uint8_t* __restrict__ cdist,
+                                                        const float* __restrict__ emean,
+                                                        const uint32_t* __restrict__ occq,
+                                                        unsigned long long occq_cap) {
+  const unsigned long long cnt = min((unsigned long long)g.st->occq_cnt, occq_cap);
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < cnt;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t idx = __ldg(&occq[q]);
+    if (voxel_visible(g, cc, eroded, cdist, emean, idx)) atomicOr(&g.vis[idx >> 5], 1u << (idx & 31));
+  }
 }
 
 namespace {
@@ -207,7 +281,8 @@ float3 tof(D3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
 }  // namespace
 
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, cudaStream_t s) {
+                uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, uint32_t* occq,
+                unsigned long long occq_cap, cudaStream_t s) {
   const D3 eye = {cam.eye[0], cam.eye[1], cam.eye[2]};
   const D3 tgt = {cam.target[0], cam.target[1], cam.target[2]};
   const D3 upw = {cam.up[0], cam.up[1], cam.up[2]};
@@ -238,9 +313,14 @@ int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* e
   cc.lt = (float)(len(nt) * h + 1e-3); cc.lb = (float)(len(nb) * h + 1e-3);
   const uint32_t nvox = (uint32_t)g.n * g.n * g.n;
   const int T = 256;
-  k_erode<<<(nvox + T - 1) / T, T, 0, s>>>(g, eroded, btmp, emean);
+  // the queue holds every voxel at most once, so it never overflows when it
+  // has room for the whole grid; otherwise each voxel's thread tests its own
+  const bool queued = occq && occq_cap >= nvox;
+  k_erode<<<(nvox / 4 + T - 1) / T, T, 0, s>>>(g, eroded, btmp, emean, queued ? occq : nullptr,
+                                               occq_cap);
   const int passes = launch_brick_dist_passes(g.log2nb, btmp, cdist, s);
-  k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded, cdist, emean);
+  if (queued) k_visible_queued<<<152 * 8, T, 0, s>>>(g, cc, eroded, cdist, emean, occq, occq_cap);
+  else k_visible<<<(nvox + T - 1) / T, T, 0, s>>>(g, cc, eroded, cdist, emean);
   return 2 + passes;
 }
 

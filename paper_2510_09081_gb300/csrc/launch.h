@@ -114,9 +114,11 @@ int launch_mips(const GridDev& g, void* mips, int fmt, const long long* lev_off,
 // Cull marks; btmp, cdist: one byte per brick (scratch; distance to a brick
 // with eroded occupancy); emean: one float per brick (mean eroded occupancy);
 // depth_max: estimated optical depth past which a voxel is culled (<= 0: the
-// default, ln(1e4) + 3).
+// default, ln(1e4) + 3); occq: scratch for the indices of the occupied voxels
+// (occq_cap entries; when fewer than n^3, every voxel's thread tests its own).
 int launch_cull(const GridDev& g, const HostCamera& cam, float alpha, uint8_t* eroded,
-                uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, cudaStream_t s);
+                uint8_t* btmp, uint8_t* cdist, float* emean, float depth_max, uint32_t* occq,
+                unsigned long long occq_cap, cudaStream_t s);
 int launch_trace(const TraceArgs& a, int K, cudaStream_t s);
 // Instrumented trace: the set bits of the three touch bitmaps into
 // st->tr_u_entries, tr_u_vertices, tr_u_voxels (which the caller cleared).

@@ -314,6 +314,7 @@ __device__ __forceinline__ void append_record(const GridDev& g, uint32_t idx, ui
 }
 
 constexpr int kWarpRecords = 256;  // pass 2: culled records a warp stages per append
+constexpr uint32_t kNoCopy = 0xffffffffu;  // cq_cnt: pass 2 copied no culled records
 
 // Append a warp's staged culled records to cq (all lanes call); records past
 // the queue's capacity are counted but dropped, which sends the repair rounds
@@ -542,13 +543,23 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t i) {
 // cursor of each listed voxel from its list start with a returning atomic.
 // Mode 1 also copies the records of unmarked voxels to the (by then unused)
 // exact-path queue, warp-staged, so that the repair rounds stream only those;
-// when they do not all fit, the repair streams every record.
+// when they do not all fit, the repair streams every record. The copy is made
+// only when under half of the fragments are culled: past that, a repair round
+// streaming every record reads less than twice the bytes the copy would write
+// in every frame, and repairs are rare (ABC pathlines at 512^3 cull 97% of their
+// fragments and need none).
 __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint32_t* __restrict__ need,
                                                  const uint32_t* __restrict__ pending) {
   if (mode == 2 && *pending == 0) return;
   __shared__ unsigned long long s_rec[8][kWarpRecords];
   unsigned long long* cq = reinterpret_cast<unsigned long long*>(g.xq);
-  const bool compact = mode == 2 && g.st->cq_cnt <= g.xq_cap;
+  bool copy = false;  // mode 1: copy the culled records (grid-uniform)
+  if (mode == 1) {
+    const unsigned long long F = g.st->F, culled = F - g.st->list_tail;
+    copy = 2 * culled < F;
+    if (!copy && blockIdx.x == 0 && threadIdx.x == 0) g.st->cq_cnt = kNoCopy;
+  }
+  const bool compact = mode == 2 && g.st->cq_cnt != kNoCopy && g.st->cq_cnt <= g.xq_cap;
   const unsigned long long* src = compact ? cq : g.rec;
   const unsigned long long cnt =
       compact ? g.st->cq_cnt : min(g.st->rec_cnt, (unsigned long long)g.rec_cap);
@@ -589,7 +600,7 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
         }
       }
     }
-    if (mode == 1) {
+    if (copy) {
       const bool keep = have && skip;
       const unsigned km = __ballot_sync(FULLW, keep);
       if (keep) srec[wcount + __popc(km & lt)] = r;
@@ -601,7 +612,7 @@ __global__ void __launch_bounds__(256) k_scatter(GridDev g, int mode, const uint
       }
     }
   }
-  if (mode == 1) {
+  if (copy) {
     __syncwarp();
     flush_culled(g, cq, srec, wcount, lane);
   }

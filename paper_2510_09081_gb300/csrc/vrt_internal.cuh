@@ -61,7 +61,7 @@ struct DevStatus {
   unsigned int repaired_voxels;
   unsigned int repair_rounds;
   unsigned int retraced_pixels;
-  unsigned int pad_;
+  unsigned int occq_cnt;             // occupied voxels the erosion queued for the cull's march
   // trace work counters (only with VRT_OPT_TRACE_COUNTERS)
   unsigned long long tr_entries;     // list entries examined
   unsigned long long tr_capsule;     // entries past the line-distance test
