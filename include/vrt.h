@@ -63,7 +63,8 @@ typedef struct {
   int32_t occ_scale;      /* occupancy codes per unit occupancy in the packed
                              word; 0 selects 32 */
   uint64_t max_fragments; /* list capacity in entries (all voxels), also the
-                             capacity of the fragment record buffer; 0 selects
+                             capacity of the fragment record and rank
+                             buffers (10 bytes per entry); 0 selects
                              0.9 (L + 2 rl + 2)(2 rl + 2)^2, at least 16,
                              entries per uploaded vertex, with L the mean
                              segment length of the vrt_upload_segments call
@@ -183,7 +184,8 @@ vrt_status vrt_update_vertices(vrt_grid g, int64_t first_vertex, int64_t n_verti
  * the last vrt_voxelize (and their polyline neighbours), and voxelization pass 1
  * (Sec. 3.1, Alg. 1 walk, Alg. 3 occupancy): for every segment and every voxel within the list
  * radius of it (r + 2^-9, decided exactly), one 32-bit atomic add of
- * (occupancy code << 16) | 1 into the voxel's packed word. */
+ * (occupancy code << 16) | 1 into the voxel's packed word; the count it returns
+ * is the fragment's rank in the voxel, kept with the fragment for pass 2. */
 vrt_status vrt_voxelize(vrt_grid g);
 
 /* Averaging occupancy pyramid (Sec. 3.1): level 0 = min(1, occupancy code sum /
@@ -193,8 +195,8 @@ vrt_status vrt_build_mips(vrt_grid g);
 /* Culling and list build (Sec. 3.2, 3.3): with p->cull = 1, mark voxels whose
  * centre sees the camera through the eroded occupancy; exclusive scan of the
  * counts of marked voxels into list offsets; voxelization pass 2 writes segment
- * ids into the lists of marked voxels. With p->cull = 0 every occupied voxel is
- * marked. Needs vrt_voxelize. */
+ * ids into the lists of marked voxels, each at the slot its rank gives. With
+ * p->cull = 0 every occupied voxel is marked. Needs vrt_voxelize. */
 vrt_status vrt_cull(vrt_grid g, const vrt_camera* cam, const vrt_render_params* p);
 
 /* Ray tracing (Sec. 3.5): one ray per pixel through the grid by 3D-DDA; in
