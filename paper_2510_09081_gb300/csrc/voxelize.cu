@@ -20,9 +20,7 @@
 // the 128-bit integer path out of the hot kernels' registers).
 //
 // Pass 1 adds (occupancy code << 16) | 1 to the voxel's packed word with a
-// 32-bit atomic (Sec. 3.1) -- on grids of side 512 and more one per distinct
-// voxel of a warp step, the increments of lanes that share the voxel summed
-// first -- and writes the fragment as an 8-byte record (voxel << 32 |
+// 32-bit atomic (Sec. 3.1) and writes the fragment as an 8-byte record (voxel << 32 |
 // segment) with its rank, the count field the atomic returned (fragments of
 // the voxel added before it), beside it. A block takes record slots for all its
 // walks' candidates with one atomic; each warp writes its fragments at the
@@ -332,7 +330,6 @@ __device__ __forceinline__ void flush_culled(const GridDev& g, unsigned long lon
   __syncwarp();
 }
 
-template <bool AGG>
 __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
                                                const float4* __restrict__ nrm,
                                                const uint32_t* __restrict__ order, long long V,
@@ -412,14 +409,12 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
   uint32_t un = 0;  // queued (uniform)
   // A fragment's rank is stored one emit later, so the latency of the
   // returning atomic that gives it overlaps a step of work: pend_r is the
-  // record slot still waiting for its rank, the rank being pend_off plus the
-  // word that lane pend_src's atomic returned (its own, without merging).
+  // record slot still waiting for its rank, the count field of the word
+  // pend_old that the lane's atomic returned.
   unsigned long long pend_r = ~0ull;
-  uint32_t pend_old = 0, pend_off = 0;
-  int pend_src = lane;
+  uint32_t pend_old = 0;
   auto flush_rank = [&]() {  // all lanes call
-    const uint32_t old = AGG ? __shfl_sync(FULLW, pend_old, pend_src) : pend_old;
-    if (pend_r < g.rec_cap) g.rank[pend_r] = (uint16_t)(old + pend_off);  // low 16 bits: count
+    if (pend_r < g.rec_cap) g.rank[pend_r] = (uint16_t)pend_old;  // low 16 bits: count
     pend_r = ~0ull;
   };
   // a kept fragment: occupancy into the packed word, record written (all lanes call)
@@ -432,18 +427,7 @@ __global__ void __launch_bounds__(256) k_pass1(const float4* __restrict__ pos,
       const uint32_t clip = __float_as_uint(p.w3.z) >> 27;
       const uint32_t inc = fragment_word(g, f3(p.w0), f3(p.w1), f3(s_n[0][wb + j]),
                                          f3(s_n[1][wb + j]), clip & 1u, clip & 2u, x, y, z, F, sq);
-      if (AGG) {
-        // lanes adding to the same voxel (neighbouring segments of the warp
-        // share voxels) sum their increments: one atomic per voxel and step
-        // and rank after the leader's count, in lane order
-        const unsigned peers = __match_any_sync(am, idx);
-        const uint32_t sum = __reduce_add_sync(peers, inc);
-        pend_src = __ffs(peers) - 1;
-        pend_off = __popc(peers & lt);
-        if (lane == pend_src) pend_old = atomicAdd(&g.word[idx], sum);
-      } else {
-        pend_old = atomicAdd(&g.word[idx], inc);
-      }
+      pend_old = atomicAdd(&g.word[idx], inc);
     }
     if (keep) {
       const unsigned long long r = rbase + wcount + __popc(am & lt);
@@ -672,12 +656,12 @@ int launch_pass1(const float4* pos, const float4* nrm, const uint32_t* order, lo
                  const GridDev& g, cudaStream_t s) {
   if (V < 2) return 0;
   const int T = 256;
-  // Grids of side 512 and more keep their packed words (512 MB) in DRAM, where
-  // merging the increments of lanes that share a voxel pays (ABC pathlines,
-  // 512^3: pass 1 7.8 -> 7.4 ms); at 256^3 the words stay in L2 and the match
-  // costs more than the atomics it saves (bundles: 2.3 -> 3.5 ms).
-  if (g.n >= 512) k_pass1<true><<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
-  else k_pass1<false><<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
+  // One atomic per fragment at every grid side: summing the increments of the
+  // lanes of a warp step that share a voxel first (a match on the voxel index)
+  // measured slower at 256^3 (bundles pass 1 2.3 -> 3.5 ms) and, since pass 1's
+  // atomics return the rank, at 512^3 too (ABC pathlines 4.70 -> 6.83 ms; it
+  // paid there while they returned nothing, 7.8 -> 7.4 ms).
+  k_pass1<<<(unsigned)((V + T - 1) / T), T, 0, s>>>(pos, nrm, order, V, g);
   k_exact1<<<152 * 4, T, 0, s>>>(pos, nrm, g);
   return 2;
 }
