@@ -522,7 +522,7 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t i) {
 // those whose voxel the cull marked, mode 2 (repair) those whose voxel's
 // `need` bit is set. Modes 0 and 1 read the voxel's list end from the scan's
 // cursor -- kCulledStart when the cull gave it no list -- and write the segment
-// id at end - 1 - rank: no atomic, and the cursor is the cull's verdict, so the
+// id at end - 1 - rank: no atomic, and the cursor carries the cull's decision, so the
 // mark is not read. The repair, whose copied records carry no rank, bumps the
 // cursor of each listed voxel from its list start with a returning atomic.
 // Mode 1 also copies the records of unmarked voxels to the (by then unused)
